@@ -1,0 +1,155 @@
+"""Sum-product belief propagation on the per-shot matching factor graph (oracle side).
+
+Test infrastructure only: nothing in the product path imports this module.
+
+For a shot with s unsatisfied detectors the factor graph F = (V, C, A) of Sec.
+"Bipartite Graph Representation" has one factor c_i per unsatisfied detector and one
+binary variable v_ij (i <= j) per decoding-graph edge; v_ij (i != j) touches c_i and c_j,
+v_ii (the edge to the boundary) touches c_i only.  Factor c_i is 1 iff exactly one of
+its variables is 1 (Eq. syndrome factors).  The prior LLR of v_ij is l_ij (Eq. priorllr).
+
+Log-domain sum-product (Sec. "Belief Propagation"), flooding schedule, all in FP64:
+  M[i, j]  = message from factor c_i to variable v_ij, M = 0 before iteration 1;
+  Q[i, k]  = l_ik + M[k, i] / alpha   (k != i), Q[i, i] = l_ii   (variable -> factor c_i);
+  M'[i, j] = -max*_{k != j} Q[i, k]  with max*(x_1..x_n) = ln sum exp(x_k), evaluated
+             directly on each leave-one-out set with a max shift; an empty set gives
+             max* = -inf and so M' = +inf;
+  lambda_ij = l_ij + (M'[i, j] + M'[j, i]) (i != j), lambda_ii = l_ii + M'[i, i]
+             (Eq. marginalization).
+One iteration = one factor update of every message from the previous ones, followed by
+the posterior; "T iterations" means T such updates.  alpha = 1 is plain BP; alpha != 1
+is the memory variant of Sec. "BP Improvements".
+
+Inference (Sec. "Forced convergence"):
+  * marginalization keeps v iff lambda_v > 0 (strict);
+  * convergence: every factor has exactly one kept variable (Sec. "Checking convergence");
+  * forced convergence, read as a global greedy: all variables sorted by lambda
+    descending (ties: smaller i, then smaller j), each accepted iff all its endpoints
+    are still unmatched.  v_ii matches i to the boundary.
+
+A `valid` mask (s x s, symmetric) removes variables from the factor graph; it only serves
+the exactness checks on tree- and cycle-shaped graphs.  Decoding always uses the full
+graph.
+"""
+import math
+
+import numpy as np
+
+
+def loo_lse(row, valid_row):
+    """out[j] = ln sum_{k != j, valid} exp(row[k]), computed per set with a max shift."""
+    s = row.shape[0]
+    out = np.full(s, -np.inf)
+    for j in range(s):
+        keep = valid_row.copy()
+        keep[j] = False
+        vals = row[keep]
+        if vals.size == 0:
+            continue
+        m = vals.max()
+        if m == -np.inf:
+            continue
+        out[j] = m + math.log(float(np.sum(np.exp(vals - m))))
+    return out
+
+
+def loo_lse_rows(Q, valid):
+    """Row-wise leave-one-out max* of a whole matrix (same definition as `loo_lse`)."""
+    s = Q.shape[0]
+    out = np.full((s, s), -np.inf)
+    eye = np.eye(s, dtype=bool)
+    for i in range(s):
+        sets = np.where(valid[i][None, :] & ~eye, Q[i][None, :], -np.inf)  # sets[j, k]
+        m = sets.max(axis=1)
+        ok = m > -np.inf
+        if not ok.any():
+            continue
+        with np.errstate(invalid="ignore", over="ignore"):
+            sh = np.exp(sets[ok] - m[ok, None])
+        out[i, ok] = m[ok] + np.log(sh.sum(axis=1))
+    return out
+
+
+def full_valid(s):
+    return np.ones((s, s), dtype=bool)
+
+
+def var_to_factor(L, M, alpha=1.0, valid=None):
+    s = L.shape[0]
+    if valid is None:
+        valid = full_valid(s)
+    with np.errstate(invalid="ignore"):
+        Q = L + M.T / alpha
+    np.fill_diagonal(Q, np.diag(L))
+    Q[~valid] = -np.inf
+    return Q
+
+
+def factor_update(L, M, alpha=1.0, valid=None):
+    s = L.shape[0]
+    if valid is None:
+        valid = full_valid(s)
+    Q = var_to_factor(L, M, alpha, valid)
+    return -loo_lse_rows(Q, valid)
+
+
+def posterior(L, M, valid=None):
+    s = L.shape[0]
+    if valid is None:
+        valid = full_valid(s)
+    with np.errstate(invalid="ignore"):
+        lam = L + (M + M.T)
+    np.fill_diagonal(lam, np.diag(L) + np.diag(M))
+    lam[~valid] = -np.inf
+    return lam
+
+
+def decide(lam):
+    """Marginalization: (kept-variable matrix, converged flag)."""
+    V = lam > 0
+    counts = V.sum(axis=1)
+    return V, bool(np.all(counts == 1))
+
+
+def matching_from(V):
+    s = V.shape[0]
+    return [(i, j) for i in range(s) for j in range(i, s) if V[i, j]]
+
+
+def forced_convergence(lam, valid=None):
+    """Global greedy matching on the posteriors; returns pairs in pick order."""
+    s = lam.shape[0]
+    if valid is None:
+        valid = full_valid(s)
+    cand = [(-float(lam[i, j]), i, j) for i in range(s) for j in range(i, s) if valid[i, j]]
+    cand.sort()
+    matched = [False] * s
+    picks = []
+    for _, i, j in cand:
+        if matched[i] or matched[j]:
+            continue
+        matched[i] = True
+        matched[j] = True
+        picks.append((i, j))
+    return picks
+
+
+def order_margin(lam):
+    """Smallest gap between two different posteriors of the upper triangle (inf if < 2)."""
+    s = lam.shape[0]
+    vals = np.sort(lam[np.triu_indices(s)])
+    vals = vals[np.isfinite(vals)]
+    if vals.size < 2:
+        return math.inf
+    return float(np.min(np.diff(vals)))
+
+
+def run_bp(L, T, alpha=1.0, valid=None):
+    """Plain T-iteration BP; returns the list of (M, lambda) after every iteration."""
+    s = L.shape[0]
+    M = np.zeros((s, s))
+    out = []
+    for _ in range(T):
+        M = factor_update(L, M, alpha, valid)
+        out.append((M, posterior(L, M, valid)))
+    return out
