@@ -1,0 +1,188 @@
+/*
+ * bp4m.h - C ABI of the GB300 (sm_103a) BP4M decoding library.
+ *
+ * The library decodes surface-code syndromes with belief propagation run on the
+ * per-shot decoding graph (one node per unsatisfied detector plus a boundary node per
+ * detector, an edge for every pair and one to the boundary), as defined in Sec.
+ * "MWPM on the surface code" and Sec. "Bipartite Graph Representation" of
+ * "Achieving Thresholds via Standalone Belief Propagation on Surface Codes"
+ * (arXiv 2603.05381).  Every decoding step runs in the library's own CUDA kernels.
+ *
+ * Conventions for every entry point:
+ *   - Return value: 0 on success, a negative BP4M_E* code on failure; the message of the
+ *     last failure on the calling thread is returned by bp4m_last_error().
+ *   - Buffers are owned by the caller.  Each buffer argument may be host memory (pageable
+ *     or pinned) or device memory of the current device; the kind is detected with
+ *     cudaPointerGetAttributes.  Host buffers are staged through library-owned device
+ *     memory.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Entry points that
+ *     return host-visible results synchronise that stream before returning.
+ *   - Graphs are owned by the library (bp4m_free_graph releases them).  A graph may be
+ *     used by one thread at a time.
+ */
+#ifndef BP4M_H
+#define BP4M_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ---- */
+#define BP4M_OK            0
+#define BP4M_EINVAL       -1   /* bad argument (null pointer, size, option) */
+#define BP4M_ENOMEM       -2   /* device or host allocation failed */
+#define BP4M_EUNSUPPORTED -3   /* valid request the library does not implement */
+#define BP4M_ETIMEOUT     -4   /* a bounded device-side wait ran out */
+#define BP4M_ECUDA        -5   /* a CUDA runtime call failed (message has the CUDA error) */
+
+/* ---- code, noise and decoder descriptions ---- */
+#define BP4M_ROTATED   0
+#define BP4M_UNROTATED 1       /* reserved: BP4M_EUNSUPPORTED */
+
+#define BP4M_MEMORY_Z  0
+
+#define BP4M_CODE_CAPACITY 0   /* i.i.d. depolarizing on data qubits: X, Y, Z with p/3 each */
+#define BP4M_CIRCUIT       1   /* rotated memory-Z circuit, uniform depolarizing noise p */
+
+#define BP4M_PRIOR_P     0     /* code capacity prior (p/(1-p))^w with the printed p */
+#define BP4M_PRIOR_2P3   1     /* code capacity prior with the X (or Z) marginal 2p/3 */
+
+/* Code: rotated surface code of distance d.  rounds = 0 with BP4M_CODE_CAPACITY;
+   with BP4M_CIRCUIT rounds = 0 means d rounds (Sec. "Numerical Results": R = d). */
+typedef struct {
+    int family;   /* BP4M_ROTATED */
+    int d;        /* odd distance >= 3 */
+    int rounds;   /* syndrome-extraction rounds (circuit only) */
+    int basis;    /* BP4M_MEMORY_Z */
+} bp4m_code;
+
+typedef struct {
+    int model;                  /* BP4M_CODE_CAPACITY or BP4M_CIRCUIT */
+    double p;                   /* physical error rate, 0 < p < 0.5 */
+    int prior_conv;             /* BP4M_PRIOR_P (default) or BP4M_PRIOR_2P3 (code capacity) */
+    int pair_through_boundary;  /* 0 (default): pair paths may not pass through the boundary */
+} bp4m_noise;
+
+#define BP4M_FP64 0
+#define BP4M_FP32 1
+
+#define BP4M_DEC_BP4M  0   /* Sec. "Belief Propagation for Matching (BP4M)" */
+#define BP4M_DEC_BP4MF 1   /* Sec. "BP4M Forced (BP4MF)"; alpha != 1 gives Memory-BP4MF */
+
+typedef struct {
+    int precision;   /* BP4M_FP64 or BP4M_FP32: message storage and arithmetic */
+    int early_exit;  /* BP4M only. 1: output the first converged iteration.
+                        0: run all iterations, keep the lightest converged candidate */
+    int decoder;     /* BP4M_DEC_BP4M or BP4M_DEC_BP4MF */
+    double alpha;    /* variable-update memory parameter (Sec. "BP Improvements"); 1 = plain */
+    int type;        /* code capacity only: 0 = X errors on the Z-check graph,
+                        1 = Z errors on the X-check graph.  Ignored for circuits. */
+} bp4m_opts;
+
+/* Aggregate counts of one sample_and_decode call (all u64). */
+typedef struct {
+    uint64_t shots;
+    uint64_t fail[3];          /* per type (X, Z) and "any"; circuits use fail[0] = fail[2] */
+    uint64_t unconverged[2];   /* shots of each type whose marginalization never converged */
+    uint64_t forced_output[2]; /* shots whose output came from forced convergence */
+    uint64_t conv_fail[2];     /* failures among shots that converged (converged LER) */
+    uint64_t iterations;       /* sum over shots and types of executed iterations */
+    uint64_t msg_updates;      /* sum over shots and types of s^2 per executed iteration */
+    uint64_t defects;          /* sum over shots and types of s */
+} bp4m_counts;
+
+typedef struct {
+    int n_types;          /* 2 for code capacity (X then Z), 1 for circuits */
+    int n_det[2];         /* detectors per type */
+    int n_words[2];       /* 32-bit syndrome words per shot and type = ceil(n_det / 32) */
+    int n_edges[2];       /* merged detector-graph edges per type */
+    int n_units;          /* sampler draws per shot (qubits or graph edges) */
+    int model;            /* BP4M_CODE_CAPACITY or BP4M_CIRCUIT */
+    int d;
+    int rounds;
+    double p;
+    int64_t table_bytes;  /* device bytes of the per-graph tables once uploaded */
+} bp4m_graph_info_t;
+
+typedef struct bp4m_graph bp4m_graph;
+
+/* Builds the static detector graph and its per-pair tables on the host (Sec. "MWPM on the
+   surface code"; the prior of Eq. (two-syn var factors) with w_ij read as a shortest-path
+   weight of edge weights ln((1-q_e)/q_e)).  No device memory is touched: the tables are
+   uploaded on the first decoding call.  *out receives a new graph. */
+int bp4m_build_graph(const bp4m_code* code, const bp4m_noise* noise, bp4m_graph** out);
+
+int bp4m_graph_info(const bp4m_graph* g, bp4m_graph_info_t* out);
+
+/* Copies a host-side table for inspection.  what: */
+#define BP4M_EXPORT_W       0  /* double [n_det][n_det]: W_ij, diagonal = to the boundary */
+#define BP4M_EXPORT_L       1  /* double [n_det][n_det]: prior LLR l_ij (Eq. priorllr) */
+#define BP4M_EXPORT_PARITY  2  /* uint8  [n_det][n_det]: observable parity of the chosen path */
+#define BP4M_EXPORT_EDGES   3  /* bp4m_edge [n_edges]: merged graph edges, canonical order */
+#define BP4M_EXPORT_THRESH  4  /* uint32 [n_units or 3]: sampler thresholds (circuit: per edge;
+                                  code capacity: t1, t2, t3) */
+typedef struct { int32_t u, v, obs, pad; double q; } bp4m_edge;
+int bp4m_graph_export(const bp4m_graph* g, int type, int what, void* out, size_t bytes);
+
+/* Draws `shots` shots with global indices first_shot .. first_shot+shots-1 and writes their
+   bit-packed syndromes, uint32 [n_types][shots][n_words] (detector j at word j>>5, bit
+   j&31), and true observable flips, uint8 [n_types][shots].  Counter-based: a shot's
+   draws depend only on (seed, stream_id, shot index). */
+int bp4m_sample(bp4m_graph* g, uint64_t first_shot, int64_t shots, uint64_t seed,
+                uint32_t stream_id, uint32_t* syndromes, uint8_t* obs_true, void* stream);
+
+/* Decodes `shots` bit-packed syndromes of one type (uint32 [shots][n_words]) with
+   `iters` BP iterations (Sec. "Belief Propagation").  Outputs per shot (any may be NULL):
+   obs_pred = predicted observable flip; converged = 1 if some iteration's marginalization
+   converged; iters_used = iterations executed.  Synchronises `stream`. */
+int bp4m_decode_batch(bp4m_graph* g, const uint32_t* syndromes, int64_t shots, int iters,
+                      const bp4m_opts* opts, uint8_t* obs_pred, uint8_t* converged,
+                      int16_t* iters_used, void* stream);
+
+/* Per-shot internals for testing, all optional (NULL = not written):
+   lambda: float or double (per opts->precision) [shots][s_cap][s_cap], posterior LLRs of
+           the last executed iteration over the shot's sorted unsatisfied detectors;
+   partner: int16 [shots][s_cap], partner[i] = j if the output pairs detector i with j,
+           i if it matches i to the boundary; entries past s are -1;
+   defects: int32 [shots], s;  flags: uint8 [shots], bit0 converged, bit1 forced
+           convergence ran, bit2 output came from forced convergence.
+   Shots with s > s_cap are decoded but their lambda/partner rows are not written. */
+typedef struct {
+    void* lambda;
+    int16_t* partner;
+    int32_t* defects;
+    uint8_t* flags;
+    int s_cap;
+} bp4m_trace;
+int bp4m_decode_trace(bp4m_graph* g, const uint32_t* syndromes, int64_t shots, int iters,
+                      const bp4m_opts* opts, uint8_t* obs_pred, const bp4m_trace* trace,
+                      void* stream);
+
+/* Samples and decodes `shots` shots (all types of the graph) and adds up failures:
+   a shot fails for a type iff the decoded observable flip differs from the sampled one.
+   p must equal the graph's p.  Work is split into device-resident batches.  *out is
+   overwritten.  Synchronises `stream`. */
+int bp4m_sample_and_decode(bp4m_graph* g, double p, int64_t shots, uint64_t seed, int iters,
+                           const bp4m_opts* opts, bp4m_counts* out, void* stream);
+
+/* Same as bp4m_sample_and_decode for the global shot range [first_shot, first_shot+shots)
+   with a Philox stream id: independent ranges can be decoded on different devices or
+   processes and their counts added. */
+int bp4m_sample_and_decode_range(bp4m_graph* g, uint64_t first_shot, int64_t shots,
+                                 uint64_t seed, uint32_t stream_id, int iters,
+                                 const bp4m_opts* opts, bp4m_counts* out, void* stream);
+
+void bp4m_free_graph(bp4m_graph* g);
+
+const char* bp4m_last_error(void);
+
+/* Library version string. */
+const char* bp4m_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BP4M_H */

@@ -1,0 +1,142 @@
+"""BP4M decoding on GB300: Python binding of libbp4m (include/bp4m.h).
+
+Every call below marshals arguments and forwards to the C ABI; all decoding work runs in
+the library's CUDA kernels.  Buffers may be torch tensors (CUDA or CPU) or numpy arrays.
+There is no CPU fallback: a missing or unloadable libbp4m.so raises.
+
+    g = Graph(d=13, model="circuit", p=0.005)
+    counts = g.sample_and_decode(shots=10**6, seed=1, iters=50)
+"""
+import ctypes
+
+import numpy as np
+
+from . import _capi
+from ._capi import (CIRCUIT, CODE_CAPACITY, DEC_BP4M, DEC_BP4MF, FP32, FP64, PRIOR_2P3, PRIOR_P,
+                    Bp4mError, check, load)
+
+__all__ = ["Graph", "Bp4mError", "load", "version", "FP32", "FP64", "DEC_BP4M", "DEC_BP4MF"]
+
+
+def version():
+    return load().bp4m_version().decode()
+
+
+def _ptr(buf):
+    """Raw address of a torch tensor or numpy array (None -> NULL)."""
+    if buf is None:
+        return None
+    if hasattr(buf, "data_ptr"):
+        if not buf.is_contiguous():
+            raise ValueError("buffers must be contiguous")
+        return buf.data_ptr()
+    if isinstance(buf, np.ndarray):
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("buffers must be C-contiguous")
+        return buf.ctypes.data
+    raise TypeError("expected a torch tensor or a numpy array, got %r" % type(buf))
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def make_opts(precision=FP32, early_exit=True, decoder="bp4m", alpha=1.0, type=0):
+    dec = {"bp4m": DEC_BP4M, "bp4mf": DEC_BP4MF}[decoder] if isinstance(decoder, str) else int(decoder)
+    prec = {"fp32": FP32, "fp64": FP64}[precision] if isinstance(precision, str) else int(precision)
+    return _capi.Opts(prec, 1 if early_exit else 0, dec, float(alpha), int(type))
+
+
+class Graph:
+    """A static detector graph with its per-pair tables (bp4m_build_graph)."""
+
+    def __init__(self, d, model="circuit", p=0.005, rounds=0, prior="p", pair_through_boundary=False):
+        lib = load()
+        m = {"code_capacity": CODE_CAPACITY, "circuit": CIRCUIT}[model] if isinstance(model, str) else model
+        code = _capi.Code(_capi.ROTATED, int(d), int(rounds), _capi.MEMORY_Z)
+        noise = _capi.Noise(m, float(p), {"p": PRIOR_P, "2p/3": PRIOR_2P3}[prior],
+                            1 if pair_through_boundary else 0)
+        h = ctypes.c_void_p()
+        check(lib.bp4m_build_graph(ctypes.byref(code), ctypes.byref(noise), ctypes.byref(h)))
+        self._h = h
+        self.d, self.model, self.p = int(d), m, float(p)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().bp4m_free_graph(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self):
+        gi = _capi.GraphInfo()
+        check(load().bp4m_graph_info(self._h, ctypes.byref(gi)))
+        return {"n_types": gi.n_types, "n_det": list(gi.n_det)[:gi.n_types],
+                "n_words": list(gi.n_words)[:gi.n_types], "n_edges": list(gi.n_edges)[:gi.n_types],
+                "n_units": gi.n_units, "model": gi.model, "d": gi.d, "rounds": gi.rounds, "p": gi.p,
+                "table_bytes": gi.table_bytes}
+
+    def export(self, what, type=0):
+        """Host copy of a table: 'W', 'L', 'parity', 'edges', 'thresholds'."""
+        info = self.info()
+        n = info["n_det"][type]
+        if what == "W" or what == "L":
+            out = np.empty((n, n), dtype=np.float64)
+            code = _capi.EXPORT_W if what == "W" else _capi.EXPORT_L
+        elif what == "parity":
+            out = np.empty((n, n), dtype=np.uint8)
+            code = _capi.EXPORT_PARITY
+        elif what == "edges":
+            arr = (_capi.Edge * info["n_edges"][type])()
+            check(load().bp4m_graph_export(self._h, type, _capi.EXPORT_EDGES, ctypes.addressof(arr),
+                                           ctypes.sizeof(arr)))
+            return [(e.u, e.v, e.obs, e.q) for e in arr]
+        elif what == "thresholds":
+            k = info["n_units"] if info["model"] == CIRCUIT else 3
+            out = np.empty(k, dtype=np.uint32)
+            code = _capi.EXPORT_THRESH
+        else:
+            raise ValueError(what)
+        check(load().bp4m_graph_export(self._h, type, code, out.ctypes.data, out.nbytes))
+        return out
+
+    def sample(self, syndromes, obs_true, first_shot=0, seed=1, stream_id=0, stream=None):
+        """bp4m_sample into caller buffers: syndromes uint32 [types][shots][words], obs uint8 [types][shots]."""
+        shots = obs_true.shape[-1]
+        check(load().bp4m_sample(self._h, int(first_shot), int(shots), int(seed), int(stream_id),
+                                 _ptr(syndromes), _ptr(obs_true), _stream(stream)))
+
+    def decode_batch(self, syndromes, iters, opts, obs_pred=None, converged=None, iters_used=None,
+                     stream=None):
+        shots = syndromes.shape[0]
+        check(load().bp4m_decode_batch(self._h, _ptr(syndromes), int(shots), int(iters), ctypes.byref(opts),
+                                       _ptr(obs_pred), _ptr(converged), _ptr(iters_used), _stream(stream)))
+
+    def decode_trace(self, syndromes, iters, opts, obs_pred, lam=None, partner=None, defects=None,
+                     flags=None, s_cap=0, stream=None):
+        tr = _capi.Trace(_ptr(lam), _ptr(partner), _ptr(defects), _ptr(flags), int(s_cap))
+        check(load().bp4m_decode_trace(self._h, _ptr(syndromes), int(syndromes.shape[0]), int(iters),
+                                       ctypes.byref(opts), _ptr(obs_pred), ctypes.byref(tr), _stream(stream)))
+
+    def sample_and_decode(self, shots, seed, iters, opts, first_shot=0, stream_id=0, stream=None):
+        c = _capi.Counts()
+        check(load().bp4m_sample_and_decode_range(self._h, int(first_shot), int(shots), int(seed),
+                                                  int(stream_id), int(iters), ctypes.byref(opts),
+                                                  ctypes.byref(c), _stream(stream)))
+        return {"shots": c.shots, "fail": list(c.fail), "unconverged": list(c.unconverged),
+                "forced_output": list(c.forced_output), "conv_fail": list(c.conv_fail),
+                "iterations": c.iterations, "msg_updates": c.msg_updates, "defects": c.defects}

@@ -1,0 +1,113 @@
+"""ctypes declarations of the C ABI in include/bp4m.h (argument marshalling only)."""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbp4m.so")
+
+BP4M_OK = 0
+ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "EUNSUPPORTED", -4: "ETIMEOUT", -5: "ECUDA"}
+
+ROTATED = 0
+MEMORY_Z = 0
+CODE_CAPACITY = 0
+CIRCUIT = 1
+PRIOR_P = 0
+PRIOR_2P3 = 1
+FP64 = 0
+FP32 = 1
+DEC_BP4M = 0
+DEC_BP4MF = 1
+EXPORT_W, EXPORT_L, EXPORT_PARITY, EXPORT_EDGES, EXPORT_THRESH = range(5)
+
+
+class Code(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_int), ("d", ctypes.c_int), ("rounds", ctypes.c_int),
+                ("basis", ctypes.c_int)]
+
+
+class Noise(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int), ("p", ctypes.c_double), ("prior_conv", ctypes.c_int),
+                ("pair_through_boundary", ctypes.c_int)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("early_exit", ctypes.c_int), ("decoder", ctypes.c_int),
+                ("alpha", ctypes.c_double), ("type", ctypes.c_int)]
+
+
+class Counts(ctypes.Structure):
+    _fields_ = [("shots", ctypes.c_uint64), ("fail", ctypes.c_uint64 * 3),
+                ("unconverged", ctypes.c_uint64 * 2), ("forced_output", ctypes.c_uint64 * 2),
+                ("conv_fail", ctypes.c_uint64 * 2), ("iterations", ctypes.c_uint64),
+                ("msg_updates", ctypes.c_uint64), ("defects", ctypes.c_uint64)]
+
+
+class GraphInfo(ctypes.Structure):
+    _fields_ = [("n_types", ctypes.c_int), ("n_det", ctypes.c_int * 2), ("n_words", ctypes.c_int * 2),
+                ("n_edges", ctypes.c_int * 2), ("n_units", ctypes.c_int), ("model", ctypes.c_int),
+                ("d", ctypes.c_int), ("rounds", ctypes.c_int), ("p", ctypes.c_double),
+                ("table_bytes", ctypes.c_int64)]
+
+
+class Edge(ctypes.Structure):
+    _fields_ = [("u", ctypes.c_int32), ("v", ctypes.c_int32), ("obs", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("q", ctypes.c_double)]
+
+
+class Trace(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_void_p), ("partner", ctypes.c_void_p), ("defects", ctypes.c_void_p),
+                ("flags", ctypes.c_void_p), ("s_cap", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "bp4m_build_graph": (ctypes.c_int, [ctypes.POINTER(Code), ctypes.POINTER(Noise), ctypes.POINTER(_P)]),
+    "bp4m_graph_info": (ctypes.c_int, [_P, ctypes.POINTER(GraphInfo)]),
+    "bp4m_graph_export": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, ctypes.c_size_t]),
+    "bp4m_sample": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
+                                   _P, _P, _P]),
+    "bp4m_decode_batch": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(Opts),
+                                         _P, _P, _P, _P]),
+    "bp4m_decode_trace": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(Opts),
+                                         _P, ctypes.POINTER(Trace), _P]),
+    "bp4m_sample_and_decode": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int64, ctypes.c_uint64,
+                                              ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(Counts), _P]),
+    "bp4m_sample_and_decode_range": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint64,
+                                                    ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(Opts),
+                                                    ctypes.POINTER(Counts), _P]),
+    "bp4m_free_graph": (None, [_P]),
+    "bp4m_last_error": (ctypes.c_char_p, []),
+    "bp4m_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def load():
+    """Loads libbp4m.so; raises if it has not been built (there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libbp4m.so is not built: run `python -c \"import __graft_entry__ as g; g.build()\"` "
+                           "or `python -m paper_2603_05381_gb300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class Bp4mError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "error"), code, msg))
+        self.code = code
+
+
+def check(rc):
+    if rc != BP4M_OK:
+        raise Bp4mError(rc, load().bp4m_last_error().decode(errors="replace"))
+    return rc

@@ -1,0 +1,621 @@
+// C ABI of the BP4M decoding library: graph lifecycle, device upload, workspaces and the
+// decode / sample entry points declared in include/bp4m.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "bp4m.h"
+#include "device.cuh"
+#include "host_graph.h"
+
+using namespace bp4m;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(e == cudaErrorMemoryAllocation ? BP4M_ENOMEM : BP4M_ECUDA, m);
+}
+
+#define CK(call)                                        \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+    return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(n, 1) * sizeof(T));
+}
+
+__global__ void finalize_kernel(const uint8_t* flags, int64_t shots, uint8_t* converged) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < shots;
+         k += (int64_t)gridDim.x * blockDim.x)
+        converged[k] = (flags[k] & F_CONVERGED) ? 1 : 0;
+}
+
+}  // namespace
+
+struct Workspace {
+    int64_t cap = 0;
+    int n_types = 1;
+    size_t words_total = 0;   // sum over types of n_words
+    uint32_t* synd = nullptr;     // [types][cap][n_words[type]] (type 1 starts at cap*n_words[0])
+    uint8_t* obs_true = nullptr;  // [types][cap]
+    uint8_t* obs_pred = nullptr;
+    uint8_t* flags = nullptr;
+    int16_t* iters = nullptr;
+    int32_t* lists = nullptr;     // [kTiers][cap]
+    int32_t* small = nullptr;     // counts[kTiers], next[kTiers], max_s
+    unsigned long long* ctr = nullptr;
+    int32_t* host_small = nullptr;  // pinned mirror of `small`
+    unsigned long long* host_ctr = nullptr;
+    void* gscratch = nullptr;
+    size_t gscratch_bytes = 0;
+    cudaEvent_t ev_small = nullptr;
+};
+
+struct bp4m_graph {
+    HostGraph host;
+    int device = -1;
+    bool uploaded = false;
+    int num_sms = 0;
+    float* L32[2] = {nullptr, nullptr};
+    double* L64[2] = {nullptr, nullptr};
+    double* W64[2] = {nullptr, nullptr};
+    uint8_t* P[2] = {nullptr, nullptr};
+    uint32_t* thr = nullptr;
+    uint32_t* uvo = nullptr;
+    uint32_t* cc_uvo = nullptr;
+    int64_t table_bytes = 0;
+    bool prepared[2] = {false, false};
+    Workspace ws;
+};
+
+namespace {
+
+int n_words_of(const bp4m_graph* g, int ty) { return (g->host.t[ty].n_det + 31) / 32; }
+
+DevTables dev_tables(const bp4m_graph* g, int ty) {
+    DevTables t;
+    t.n_det = g->host.t[ty].n_det;
+    t.n_words = n_words_of(g, ty);
+    t.L32 = g->L32[ty];
+    t.L64 = g->L64[ty];
+    t.W64 = g->W64[ty];
+    t.P = g->P[ty];
+    return t;
+}
+
+int ensure_uploaded(bp4m_graph* g) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (g->uploaded) {
+        if (dev != g->device) return fail(BP4M_EINVAL, "graph was uploaded to another device");
+        return BP4M_OK;
+    }
+    g->device = dev;
+    CK(cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    const HostGraph& h = g->host;
+    g->table_bytes = 0;
+    for (int ty = 0; ty < h.n_types; ++ty) {
+        const size_t nn = (size_t)h.t[ty].n_det * h.t[ty].n_det;
+        std::vector<float> l32(nn);
+        for (size_t k = 0; k < nn; ++k) {
+            const double v = h.t[ty].L[k];
+            // a disconnected pair keeps a finite, overwhelmingly unlikely prior
+            l32[k] = std::isinf(v) ? -1.0e30f : (float)v;
+        }
+        std::vector<double> l64(h.t[ty].L);
+        for (double& v : l64)
+            if (std::isinf(v)) v = -1.0e300;
+        CK(dalloc(&g->L32[ty], nn));
+        CK(dalloc(&g->L64[ty], nn));
+        CK(dalloc(&g->W64[ty], nn));
+        CK(dalloc(&g->P[ty], nn));
+        CK(cudaMemcpy(g->L32[ty], l32.data(), nn * sizeof(float), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(g->L64[ty], l64.data(), nn * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(g->W64[ty], h.t[ty].W.data(), nn * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(g->P[ty], h.t[ty].P.data(), nn, cudaMemcpyHostToDevice));
+        g->table_bytes += (int64_t)nn * (sizeof(float) + 2 * sizeof(double) + 1);
+    }
+    auto pack = [](int u, int v, int obs) -> uint32_t {
+        return (uint32_t)u | ((uint32_t)v << 15) | ((uint32_t)(obs & 1) << 31);
+    };
+    if (h.model == BP4M_CIRCUIT) {
+        const auto& e = h.t[0].edges;
+        std::vector<uint32_t> uvo(e.size());
+        for (size_t k = 0; k < e.size(); ++k) uvo[k] = pack(e[k].u, e[k].v, e[k].obs);
+        CK(dalloc(&g->thr, e.size()));
+        CK(dalloc(&g->uvo, e.size()));
+        CK(cudaMemcpy(g->thr, h.thr.data(), e.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(g->uvo, uvo.data(), e.size() * 4, cudaMemcpyHostToDevice));
+        g->table_bytes += (int64_t)e.size() * 8;
+    } else {
+        std::vector<uint32_t> cc(2 * (size_t)h.n_units);
+        for (int ty = 0; ty < 2; ++ty)
+            for (int q = 0; q < h.n_units; ++q)
+                cc[(size_t)ty * h.n_units + q] = pack(h.cc_u[ty][q], h.cc_v[ty][q], h.cc_obs[ty][q]);
+        CK(dalloc(&g->cc_uvo, cc.size()));
+        CK(cudaMemcpy(g->cc_uvo, cc.data(), cc.size() * 4, cudaMemcpyHostToDevice));
+        g->table_bytes += (int64_t)cc.size() * 4;
+    }
+    g->uploaded = true;
+    return BP4M_OK;
+}
+
+void free_ws(Workspace& w) {
+    cudaFree(w.synd);
+    cudaFree(w.obs_true);
+    cudaFree(w.obs_pred);
+    cudaFree(w.flags);
+    cudaFree(w.iters);
+    cudaFree(w.lists);
+    cudaFree(w.small);
+    cudaFree(w.ctr);
+    cudaFree(w.gscratch);
+    cudaFreeHost(w.host_small);
+    cudaFreeHost(w.host_ctr);
+    if (w.ev_small) cudaEventDestroy(w.ev_small);
+    w = Workspace();
+}
+
+int ensure_ws(bp4m_graph* g, int64_t cap) {
+    Workspace& w = g->ws;
+    if (w.cap >= cap && w.small) return BP4M_OK;
+    const int nt = g->host.n_types;
+    void* gs = w.gscratch;
+    size_t gsb = w.gscratch_bytes;
+    w.gscratch = nullptr;
+    free_ws(w);
+    w.gscratch = gs;
+    w.gscratch_bytes = gsb;
+    w.cap = cap;
+    w.n_types = nt;
+    w.words_total = 0;
+    for (int ty = 0; ty < nt; ++ty) w.words_total += n_words_of(g, ty);
+    CK(dalloc(&w.synd, (size_t)cap * w.words_total));
+    CK(dalloc(&w.obs_true, (size_t)cap * nt));
+    CK(dalloc(&w.obs_pred, (size_t)cap * nt));
+    CK(dalloc(&w.flags, (size_t)cap * nt));
+    CK(dalloc(&w.iters, (size_t)cap * nt));
+    CK(dalloc(&w.lists, (size_t)cap * kTiers));
+    CK(dalloc(&w.small, 2 * kTiers + 1));
+    CK(dalloc(&w.ctr, C_NUM));
+    CK(cudaMallocHost(reinterpret_cast<void**>(&w.host_small), (2 * kTiers + 1) * sizeof(int32_t)));
+    CK(cudaMallocHost(reinterpret_cast<void**>(&w.host_ctr), C_NUM * sizeof(unsigned long long)));
+    CK(cudaEventCreateWithFlags(&w.ev_small, cudaEventDisableTiming));
+    return BP4M_OK;
+}
+
+int ensure_gscratch(bp4m_graph* g, size_t bytes) {
+    Workspace& w = g->ws;
+    if (w.gscratch_bytes >= bytes) return BP4M_OK;
+    cudaFree(w.gscratch);
+    w.gscratch = nullptr;
+    w.gscratch_bytes = 0;
+    CK(cudaMalloc(&w.gscratch, bytes));
+    w.gscratch_bytes = bytes;
+    return BP4M_OK;
+}
+
+int check_opts(const bp4m_graph* g, const bp4m_opts* o, int iters) {
+    if (!o) return fail(BP4M_EINVAL, "opts is NULL");
+    if (o->precision != BP4M_FP64 && o->precision != BP4M_FP32)
+        return fail(BP4M_EINVAL, "precision must be BP4M_FP64 or BP4M_FP32");
+    if (o->decoder != BP4M_DEC_BP4M && o->decoder != BP4M_DEC_BP4MF)
+        return fail(BP4M_EINVAL, "unknown decoder");
+    if (!(o->alpha > 0.0)) return fail(BP4M_EINVAL, "alpha must be positive");
+    if (iters < 1 || iters > 30000) return fail(BP4M_EINVAL, "iters must be in [1, 30000]");
+    if (g->host.n_types == 2 && (o->type < 0 || o->type > 1))
+        return fail(BP4M_EINVAL, "type must be 0 (X) or 1 (Z)");
+    return BP4M_OK;
+}
+
+// Decodes `shots` device-resident syndromes of type `ty`; results go to the given device
+// arrays (obs_pred / flags / iters are required here).
+int decode_device(bp4m_graph* g, int ty, const uint32_t* synd, int64_t shots, int T,
+                  const bp4m_opts* o, uint8_t* obs_pred, uint8_t* flags, int16_t* iters,
+                  const bp4m_trace* tr, cudaStream_t st) {
+    Workspace& w = g->ws;
+    const int prec = o->precision == BP4M_FP64 ? 0 : 1;
+    if (!g->prepared[prec]) {
+        CK(prepare_decode_kernels(prec));
+        g->prepared[prec] = true;
+    }
+    const TierPlan plan = tier_plan(prec);
+    CK(cudaMemsetAsync(w.small, 0, (2 * kTiers + 1) * sizeof(int32_t), st));
+    CK(launch_classify(synd, shots, n_words_of(g, ty), plan, w.lists, w.small, w.small + 2 * kTiers,
+                       obs_pred, flags, iters, tr ? tr->defects : nullptr, st));
+    CK(cudaMemcpyAsync(w.host_small, w.small, (2 * kTiers + 1) * sizeof(int32_t),
+                       cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(w.ev_small, st));
+    DecodeArgs a;
+    a.tb = dev_tables(g, ty);
+    a.synd = synd;
+    a.shots = shots;
+    a.T = T;
+    a.early_exit = o->early_exit ? 1 : 0;
+    a.decoder = o->decoder;
+    a.alpha = o->alpha;
+    a.obs_pred = obs_pred;
+    a.flags = flags;
+    a.iters = iters;
+    a.ctr = w.ctr;
+    if (tr) {
+        a.tr_lambda = tr->lambda;
+        a.tr_partner = tr->partner;
+        a.tr_defects = tr->defects;
+        a.s_cap = tr->s_cap;
+    }
+    for (int tier = 1; tier < kGlobalTier; ++tier) {
+        a.list = w.lists + (size_t)tier * shots;
+        a.count = w.small + tier;
+        a.next = w.small + kTiers + tier;
+        CK(launch_decode_tier(prec, tier, a, g->num_sms, st));
+    }
+    CK(cudaEventSynchronize(w.ev_small));
+    const int n_glob = w.host_small[kGlobalTier];
+    if (n_glob > 0) {
+        const int max_s = w.host_small[2 * kTiers];
+        const int gsmax = (max_s + 63) / 64 * 64;
+        const size_t esz = prec == 0 ? sizeof(double) : sizeof(float);
+        const size_t slot_bytes = (size_t)3 * gsmax * gsmax * esz;
+        int slots = std::min(n_glob, 2 * g->num_sms);
+        const size_t budget = (size_t)16 << 30;
+        while (slots > 1 && (size_t)slots * slot_bytes > budget) --slots;
+        int rc = ensure_gscratch(g, (size_t)slots * slot_bytes);
+        if (rc) return rc;
+        a.list = w.lists + (size_t)kGlobalTier * shots;
+        a.count = w.small + kGlobalTier;
+        a.next = w.small + kTiers + kGlobalTier;
+        a.gscratch = w.gscratch;
+        a.gslot_elems = (int64_t)gsmax * gsmax;
+        a.gsmax = gsmax;
+        CK(launch_decode_global(prec, a, slots, st));
+    }
+    return BP4M_OK;
+}
+
+void fill_counts(const unsigned long long* c, int n_types, bp4m_counts* out) {
+    std::memset(out, 0, sizeof(*out));
+    out->shots = c[C_SHOTS];
+    out->fail[0] = c[C_FAIL_X];
+    out->fail[1] = n_types == 2 ? c[C_FAIL_Z] : 0;
+    out->fail[2] = c[C_FAIL_ANY];
+    out->unconverged[0] = c[C_UNCONV_X];
+    out->unconverged[1] = c[C_UNCONV_Z];
+    out->forced_output[0] = c[C_FORCED_X];
+    out->forced_output[1] = c[C_FORCED_Z];
+    out->conv_fail[0] = c[C_CONVFAIL_X];
+    out->conv_fail[1] = c[C_CONVFAIL_Z];
+    out->iterations = c[C_ITERS];
+    out->msg_updates = c[C_MSGS];
+    out->defects = c[C_DEFECTS];
+}
+
+int sample_into(bp4m_graph* g, uint64_t first_shot, int64_t shots, uint64_t seed, uint32_t sid,
+                uint32_t* synd_dev, uint8_t* obs_dev, cudaStream_t st) {
+    const HostGraph& h = g->host;
+    SampleArgs a;
+    a.first_shot = first_shot;
+    a.shots = shots;
+    a.seed = seed;
+    a.stream_id = sid;
+    a.n_units = h.n_units;
+    a.n_types = h.n_types;
+    for (int ty = 0; ty < h.n_types; ++ty) {
+        a.n_det[ty] = h.t[ty].n_det;
+        a.n_words[ty] = n_words_of(g, ty);
+    }
+    a.synd = synd_dev;
+    a.obs = obs_dev;
+    if (h.model == BP4M_CIRCUIT) {
+        a.thr = g->thr;
+        a.uvo = g->uvo;
+        CK(launch_sample_circuit(a, st));
+    } else {
+        a.cc_uvo = g->cc_uvo;
+        for (int k = 0; k < 3; ++k) a.cc_thr[k] = h.cc_thr[k];
+        CK(launch_sample_code_capacity(a, st));
+    }
+    return BP4M_OK;
+}
+
+constexpr int64_t kBatch = (int64_t)1 << 20;
+
+}  // namespace
+
+extern "C" {
+
+const char* bp4m_last_error(void) { return g_last_error.c_str(); }
+
+const char* bp4m_version(void) { return "bp4m-gb300 0.1 (sm_103a)"; }
+
+int bp4m_build_graph(const bp4m_code* code, const bp4m_noise* noise, bp4m_graph** out) {
+    if (!code || !noise || !out) return fail(BP4M_EINVAL, "null argument");
+    *out = nullptr;
+    bp4m_graph* g = new (std::nothrow) bp4m_graph();
+    if (!g) return fail(BP4M_ENOMEM, "host allocation failed");
+    std::string err;
+    int rc;
+    try {
+        rc = build_host_graph(*code, *noise, g->host, err);
+    } catch (const std::bad_alloc&) {
+        rc = BP4M_ENOMEM;
+        err = "host allocation failed while building the graph";
+    }
+    if (rc != BP4M_OK) {
+        delete g;
+        return fail(rc, err);
+    }
+    *out = g;
+    return BP4M_OK;
+}
+
+int bp4m_graph_info(const bp4m_graph* g, bp4m_graph_info_t* out) {
+    if (!g || !out) return fail(BP4M_EINVAL, "null argument");
+    std::memset(out, 0, sizeof(*out));
+    const HostGraph& h = g->host;
+    out->n_types = h.n_types;
+    for (int ty = 0; ty < h.n_types; ++ty) {
+        out->n_det[ty] = h.t[ty].n_det;
+        out->n_words[ty] = (h.t[ty].n_det + 31) / 32;
+        out->n_edges[ty] = (int)h.t[ty].edges.size();
+    }
+    out->n_units = h.n_units;
+    out->model = h.model;
+    out->d = h.d;
+    out->rounds = h.rounds;
+    out->p = h.p;
+    int64_t tb = 0;
+    for (int ty = 0; ty < h.n_types; ++ty)
+        tb += (int64_t)h.t[ty].n_det * h.t[ty].n_det * (int64_t)(sizeof(float) + 2 * sizeof(double) + 1);
+    tb += h.model == BP4M_CIRCUIT ? (int64_t)h.n_units * 8 : (int64_t)h.n_units * 8;
+    out->table_bytes = tb;
+    return BP4M_OK;
+}
+
+int bp4m_graph_export(const bp4m_graph* g, int type, int what, void* out, size_t bytes) {
+    if (!g || !out) return fail(BP4M_EINVAL, "null argument");
+    const HostGraph& h = g->host;
+    if (type < 0 || type >= h.n_types) return fail(BP4M_EINVAL, "type out of range");
+    const TypeTables& t = h.t[type];
+    const size_t nn = (size_t)t.n_det * t.n_det;
+    switch (what) {
+        case BP4M_EXPORT_W:
+            if (bytes < nn * 8) return fail(BP4M_EINVAL, "buffer too small");
+            std::memcpy(out, t.W.data(), nn * 8);
+            return BP4M_OK;
+        case BP4M_EXPORT_L:
+            if (bytes < nn * 8) return fail(BP4M_EINVAL, "buffer too small");
+            std::memcpy(out, t.L.data(), nn * 8);
+            return BP4M_OK;
+        case BP4M_EXPORT_PARITY:
+            if (bytes < nn) return fail(BP4M_EINVAL, "buffer too small");
+            std::memcpy(out, t.P.data(), nn);
+            return BP4M_OK;
+        case BP4M_EXPORT_EDGES: {
+            if (bytes < t.edges.size() * sizeof(bp4m_edge)) return fail(BP4M_EINVAL, "buffer too small");
+            bp4m_edge* e = static_cast<bp4m_edge*>(out);
+            for (size_t k = 0; k < t.edges.size(); ++k)
+                e[k] = bp4m_edge{t.edges[k].u, t.edges[k].v, t.edges[k].obs, 0, t.edges[k].q};
+            return BP4M_OK;
+        }
+        case BP4M_EXPORT_THRESH:
+            if (h.model == BP4M_CIRCUIT) {
+                if (bytes < h.thr.size() * 4) return fail(BP4M_EINVAL, "buffer too small");
+                std::memcpy(out, h.thr.data(), h.thr.size() * 4);
+            } else {
+                if (bytes < 12) return fail(BP4M_EINVAL, "buffer too small");
+                std::memcpy(out, h.cc_thr, 12);
+            }
+            return BP4M_OK;
+        default:
+            return fail(BP4M_EINVAL, "unknown export");
+    }
+}
+
+int bp4m_sample(bp4m_graph* g, uint64_t first_shot, int64_t shots, uint64_t seed,
+                uint32_t stream_id, uint32_t* syndromes, uint8_t* obs_true, void* stream) {
+    if (!g || !syndromes || !obs_true) return fail(BP4M_EINVAL, "null argument");
+    if (shots < 0 || shots > ((int64_t)1 << 31)) return fail(BP4M_EINVAL, "shots out of range");
+    if (shots == 0) return BP4M_OK;
+    int rc = ensure_uploaded(g);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool dev_s = is_device_ptr(syndromes), dev_o = is_device_ptr(obs_true);
+    const int nt = g->host.n_types;
+    size_t words = 0;
+    for (int ty = 0; ty < nt; ++ty) words += n_words_of(g, ty);
+    for (int64_t off = 0; off < shots; off += kBatch) {
+        const int64_t nb = std::min(kBatch, shots - off);
+        // layout per batch is [types][nb][words]; assemble the caller's [types][shots] layout
+        uint32_t* sd;
+        uint8_t* od;
+        const bool direct = dev_s && dev_o && nb == shots;
+        if (direct) {
+            sd = syndromes;
+            od = obs_true;
+        } else {
+            rc = ensure_ws(g, std::max<int64_t>(nb, g->ws.cap));
+            if (rc) return rc;
+            sd = g->ws.synd;
+            od = g->ws.obs_true;
+        }
+        rc = sample_into(g, first_shot + (uint64_t)off, nb, seed, stream_id, sd, od, st);
+        if (rc) return rc;
+        if (!direct) {
+            size_t woff = 0;
+            for (int ty = 0; ty < nt; ++ty) {
+                const int nw = n_words_of(g, ty);
+                uint32_t* dst = syndromes + (size_t)shots * woff + (size_t)off * nw;
+                CK(cudaMemcpyAsync(dst, sd + (size_t)nb * woff, (size_t)nb * nw * 4,
+                                   cudaMemcpyDefault, st));
+                CK(cudaMemcpyAsync(obs_true + (size_t)ty * shots + off, od + (size_t)ty * nb, nb,
+                                   cudaMemcpyDefault, st));
+                woff += nw;
+            }
+            CK(cudaStreamSynchronize(st));
+        }
+    }
+    CK(cudaStreamSynchronize(st));
+    return BP4M_OK;
+}
+
+static int decode_common(bp4m_graph* g, const uint32_t* syndromes, int64_t shots, int iters,
+                         const bp4m_opts* opts, uint8_t* obs_pred, uint8_t* converged,
+                         int16_t* iters_used, const bp4m_trace* tr, void* stream) {
+    if (!g || !syndromes) return fail(BP4M_EINVAL, "null argument");
+    if (shots < 0 || shots > ((int64_t)1 << 31)) return fail(BP4M_EINVAL, "shots out of range");
+    int rc = check_opts(g, opts, iters);
+    if (rc) return rc;
+    if (tr && (tr->s_cap < 1 || tr->s_cap > 4096)) return fail(BP4M_EINVAL, "trace s_cap out of range");
+    if (shots == 0) return BP4M_OK;
+    rc = ensure_uploaded(g);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int ty = g->host.n_types == 2 ? opts->type : 0;
+    const int nw = n_words_of(g, ty);
+    const bool dev_in = is_device_ptr(syndromes);
+    if (tr) {
+        if ((tr->lambda && !is_device_ptr(tr->lambda)) || (tr->partner && !is_device_ptr(tr->partner)) ||
+            (tr->defects && !is_device_ptr(tr->defects)) || (tr->flags && !is_device_ptr(tr->flags)))
+            return fail(BP4M_EINVAL, "trace buffers must be device memory");
+        if (shots > kBatch) return fail(BP4M_EINVAL, "traced decodes take at most 2^20 shots");
+    }
+    for (int64_t off = 0; off < shots; off += kBatch) {
+        const int64_t nb = std::min(kBatch, shots - off);
+        rc = ensure_ws(g, std::max<int64_t>(nb, g->ws.cap));
+        if (rc) return rc;
+        Workspace& w = g->ws;
+        const uint32_t* sd = syndromes + (size_t)off * nw;
+        if (!dev_in) {
+            CK(cudaMemcpyAsync(w.synd, sd, (size_t)nb * nw * 4, cudaMemcpyHostToDevice, st));
+            sd = w.synd;
+        }
+        rc = decode_device(g, ty, sd, nb, iters, opts, w.obs_pred, w.flags, w.iters, tr, st);
+        if (rc) return rc;
+        if (tr && tr->flags) CK(cudaMemcpyAsync(tr->flags, w.flags, nb, cudaMemcpyDeviceToDevice, st));
+        if (obs_pred) CK(cudaMemcpyAsync(obs_pred + off, w.obs_pred, nb, cudaMemcpyDefault, st));
+        if (iters_used) CK(cudaMemcpyAsync(iters_used + off, w.iters, nb * 2, cudaMemcpyDefault, st));
+        if (converged) {
+            if (is_device_ptr(converged)) {
+                finalize_kernel<<<(int)std::min<int64_t>((nb + 255) / 256, 4096), 256, 0, st>>>(
+                    w.flags, nb, converged + off);
+                CK(cudaGetLastError());
+            } else {
+                std::vector<uint8_t> fl(nb);
+                CK(cudaMemcpyAsync(fl.data(), w.flags, nb, cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                for (int64_t k = 0; k < nb; ++k) converged[off + k] = (fl[k] & F_CONVERGED) ? 1 : 0;
+            }
+        }
+        CK(cudaStreamSynchronize(st));
+    }
+    return BP4M_OK;
+}
+
+int bp4m_decode_batch(bp4m_graph* g, const uint32_t* syndromes, int64_t shots, int iters,
+                      const bp4m_opts* opts, uint8_t* obs_pred, uint8_t* converged,
+                      int16_t* iters_used, void* stream) {
+    return decode_common(g, syndromes, shots, iters, opts, obs_pred, converged, iters_used, nullptr,
+                         stream);
+}
+
+int bp4m_decode_trace(bp4m_graph* g, const uint32_t* syndromes, int64_t shots, int iters,
+                      const bp4m_opts* opts, uint8_t* obs_pred, const bp4m_trace* trace,
+                      void* stream) {
+    if (!trace) return fail(BP4M_EINVAL, "trace is NULL");
+    return decode_common(g, syndromes, shots, iters, opts, obs_pred, nullptr, nullptr, trace, stream);
+}
+
+int bp4m_sample_and_decode_range(bp4m_graph* g, uint64_t first_shot, int64_t shots, uint64_t seed,
+                                 uint32_t stream_id, int iters, const bp4m_opts* opts,
+                                 bp4m_counts* out, void* stream) {
+    if (!g || !out) return fail(BP4M_EINVAL, "null argument");
+    if (shots < 0) return fail(BP4M_EINVAL, "shots must be non-negative");
+    int rc = check_opts(g, opts, iters);
+    if (rc) return rc;
+    std::memset(out, 0, sizeof(*out));
+    if (shots == 0) return BP4M_OK;
+    rc = ensure_uploaded(g);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t cap = std::min(kBatch, shots);
+    rc = ensure_ws(g, std::max<int64_t>(cap, g->ws.cap));
+    if (rc) return rc;
+    Workspace& w = g->ws;
+    const int nt = g->host.n_types;
+    CK(cudaMemsetAsync(w.ctr, 0, C_NUM * sizeof(unsigned long long), st));
+    for (int64_t off = 0; off < shots; off += cap) {
+        const int64_t nb = std::min(cap, shots - off);
+        rc = sample_into(g, first_shot + (uint64_t)off, nb, seed, stream_id, w.synd, w.obs_true, st);
+        if (rc) return rc;
+        size_t woff = 0;
+        for (int ty = 0; ty < nt; ++ty) {
+            bp4m_opts o = *opts;
+            o.type = ty;
+            rc = decode_device(g, ty, w.synd + (size_t)nb * woff, nb, iters, &o, w.obs_pred + (size_t)ty * nb,
+                               w.flags + (size_t)ty * nb, w.iters + (size_t)ty * nb, nullptr, st);
+            if (rc) return rc;
+            woff += n_words_of(g, ty);
+        }
+        CK(launch_count(w.obs_true, w.obs_pred, w.flags, nb, nt, w.ctr, st));
+    }
+    CK(cudaMemcpyAsync(w.host_ctr, w.ctr, C_NUM * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (w.host_ctr[C_ERRORS]) return fail(BP4M_ECUDA, "decoder kernels rejected shots (internal size check)");
+    fill_counts(w.host_ctr, nt, out);
+    return BP4M_OK;
+}
+
+int bp4m_sample_and_decode(bp4m_graph* g, double p, int64_t shots, uint64_t seed, int iters,
+                           const bp4m_opts* opts, bp4m_counts* out, void* stream) {
+    if (!g) return fail(BP4M_EINVAL, "null graph");
+    if (p != g->host.p) return fail(BP4M_EINVAL, "p differs from the graph's p; build a graph for it");
+    return bp4m_sample_and_decode_range(g, 0, shots, seed, 0, iters, opts, out, stream);
+}
+
+void bp4m_free_graph(bp4m_graph* g) {
+    if (!g) return;
+    if (g->uploaded) {
+        for (int ty = 0; ty < 2; ++ty) {
+            cudaFree(g->L32[ty]);
+            cudaFree(g->L64[ty]);
+            cudaFree(g->W64[ty]);
+            cudaFree(g->P[ty]);
+        }
+        cudaFree(g->thr);
+        cudaFree(g->uvo);
+        cudaFree(g->cc_uvo);
+        free_ws(g->ws);
+    }
+    delete g;
+}
+
+}  // extern "C"

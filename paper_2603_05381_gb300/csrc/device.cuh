@@ -1,0 +1,115 @@
+// Internal interface between the C-ABI layer and the CUDA kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bp4m {
+
+// Device copy of one type's per-pair tables (row-major n_det x n_det, diagonal = boundary).
+struct DevTables {
+    int n_det = 0;
+    int n_words = 0;
+    const float* L32 = nullptr;   // prior LLR, FP32
+    const double* L64 = nullptr;  // prior LLR, FP64
+    const double* W64 = nullptr;  // shortest-path weight, FP64 (candidate weights)
+    const uint8_t* P = nullptr;   // observable parity of the path
+};
+
+// Counter slots (unsigned long long) in the device counter block.
+enum CounterSlot {
+    C_SHOTS = 0,
+    C_FAIL_X, C_FAIL_Z, C_FAIL_ANY,
+    C_UNCONV_X, C_UNCONV_Z,
+    C_FORCED_X, C_FORCED_Z,
+    C_CONVFAIL_X, C_CONVFAIL_Z,
+    C_ITERS, C_MSGS, C_DEFECTS,
+    C_ERRORS,          // shots the kernels refused (internal consistency checks)
+    C_NUM
+};
+
+// Per-shot result flags.
+enum : uint8_t { F_CONVERGED = 1, F_FORCED_RAN = 2, F_FROM_FORCED = 4 };
+
+// Number of s tiers and the per-tier bookkeeping in the workspace.
+constexpr int kTiers = 6;      // tier 0: s == 0 (done in classify), 1..4 shared memory, 5 global
+constexpr int kGlobalTier = 5;
+
+struct TierPlan {
+    int smax[kTiers];  // inclusive upper bound of s for the tier (tier 5: unbounded)
+};
+
+struct DecodeArgs {
+    DevTables tb;
+    const uint32_t* synd = nullptr;  // [shots][n_words]
+    int64_t shots = 0;
+    const int32_t* list = nullptr;   // this tier's shot indices
+    const int32_t* count = nullptr;  // number of entries in `list`
+    int32_t* next = nullptr;         // work-stealing counter
+    int T = 0;
+    int early_exit = 1;
+    int decoder = 0;                 // 0 = BP4M, 1 = BP4MF
+    double alpha = 1.0;
+    int pitch = 0;                   // shared-memory row pitch in elements
+    // outputs (any may be null)
+    uint8_t* obs_pred = nullptr;
+    uint8_t* flags = nullptr;
+    int16_t* iters = nullptr;
+    unsigned long long* ctr = nullptr;
+    // trace (tests): lambda [shots][s_cap][s_cap] of the compute type, partner [shots][s_cap]
+    void* tr_lambda = nullptr;
+    int16_t* tr_partner = nullptr;
+    int32_t* tr_defects = nullptr;
+    int s_cap = 0;
+    // global tier: scratch slots
+    void* gscratch = nullptr;
+    int64_t gslot_elems = 0;         // elements per slot for each of the three matrices
+    int gsmax = 0;                   // largest s a slot holds
+};
+
+struct SampleArgs {
+    uint64_t first_shot = 0;
+    int64_t shots = 0;
+    uint64_t seed = 0;
+    uint32_t stream_id = 0;
+    int n_units = 0;
+    int n_types = 1;
+    int n_det[2] = {0, 0};
+    int n_words[2] = {0, 0};
+    // circuit: per edge threshold and packed (u | v << 15 | obs << 31)
+    const uint32_t* thr = nullptr;
+    const uint32_t* uvo = nullptr;
+    // code capacity: per qubit and type packed (u | v << 15 | obs << 31); thresholds t1..t3
+    const uint32_t* cc_uvo = nullptr;  // [2][n_units]
+    uint32_t cc_thr[3] = {0, 0, 0};
+    uint32_t* synd = nullptr;          // [n_types][shots][n_words]
+    uint8_t* obs = nullptr;            // [n_types][shots]
+};
+
+// ---- launchers (kernels_*.cu) ----
+cudaError_t launch_sample_circuit(const SampleArgs& a, cudaStream_t st);
+cudaError_t launch_sample_code_capacity(const SampleArgs& a, cudaStream_t st);
+
+// classify: per shot s = popcount; s == 0 results are written directly; the others are
+// appended to their tier's list.  counts[kTiers], max_s (int) must be zeroed before.
+cudaError_t launch_classify(const uint32_t* synd, int64_t shots, int n_words,
+                            const TierPlan& plan, int32_t* lists /*[kTiers][shots]*/,
+                            int32_t* counts, int32_t* max_s, uint8_t* obs_pred, uint8_t* flags,
+                            int16_t* iters, int32_t* tr_defects, cudaStream_t st);
+
+// Launch the decoding kernel of shared-memory tier `tier` (1..4) for precision
+// (0 = FP64, 1 = FP32).  Returns cudaSuccess if the tier is empty by construction.
+cudaError_t launch_decode_tier(int precision, int tier, const DecodeArgs& a, int num_sms,
+                               cudaStream_t st);
+// Global-memory tier.  `slots` CTAs each own one scratch slot.
+cudaError_t launch_decode_global(int precision, const DecodeArgs& a, int slots,
+                                 cudaStream_t st);
+// Shared-memory tier plan for a precision.
+TierPlan tier_plan(int precision);
+size_t tier_smem_bytes(int precision, int tier, int* pitch_out);
+cudaError_t prepare_decode_kernels(int precision);
+
+cudaError_t launch_count(const uint8_t* obs_true, const uint8_t* obs_pred, const uint8_t* flags,
+                         int64_t shots, int n_types, unsigned long long* ctr, cudaStream_t st);
+
+}  // namespace bp4m
