@@ -92,6 +92,8 @@ typedef struct {
     uint64_t iterations;       /* sum over shots and types of executed iterations */
     uint64_t msg_updates;      /* sum over shots and types of s^2 per executed iteration */
     uint64_t defects;          /* sum over shots and types of s */
+    uint64_t forced_runs;      /* forced-convergence runs */
+    uint64_t forced_rounds;    /* rounds of locally dominant choices summed over those runs */
 } bp4m_counts;
 
 typedef struct {
@@ -174,6 +176,22 @@ int bp4m_sample_and_decode(bp4m_graph* g, double p, int64_t shots, uint64_t seed
 int bp4m_sample_and_decode_range(bp4m_graph* g, uint64_t first_shot, int64_t shots,
                                  uint64_t seed, uint32_t stream_id, int iters,
                                  const bp4m_opts* opts, bp4m_counts* out, void* stream);
+
+/* Kernel timing for measurement.  While enabled, every kernel the library launches for
+   this graph is bracketed by CUDA events recorded on the launch stream, and the
+   algorithmic message updates of each decoding tier are counted.  Enabling resets the
+   accumulators; reading synchronises the events.  Slots: 0 = defect classification,
+   1..5 = shared-memory decode tiers (s <= 32, 64, 96, 128, 160 in FP32; 32, 64, 112 in
+   FP64), 6 = global-memory decode tier, 7 = sampler, 8 = failure counting. */
+#define BP4M_PROF_SLOTS 9
+typedef struct {
+    int64_t launches[BP4M_PROF_SLOTS];
+    double ms[BP4M_PROF_SLOTS];                /* summed event-timed durations */
+    uint64_t msg_updates[BP4M_PROF_SLOTS];     /* decode tiers: sum of s^2 per executed iteration */
+    uint64_t shots[BP4M_PROF_SLOTS];           /* decode tiers: shots decoded */
+} bp4m_profile_t;
+int bp4m_profile_enable(bp4m_graph* g, int on);
+int bp4m_profile_read(bp4m_graph* g, bp4m_profile_t* out);
 
 void bp4m_free_graph(bp4m_graph* g);
 

@@ -132,6 +132,17 @@ class Graph:
         check(load().bp4m_decode_trace(self._h, _ptr(syndromes), int(syndromes.shape[0]), int(iters),
                                        ctypes.byref(opts), _ptr(obs_pred), ctypes.byref(tr), _stream(stream)))
 
+    def profile_enable(self, on=True):
+        """Start (and reset) or stop event timing of every kernel launch of this graph."""
+        check(load().bp4m_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        """Per slot (classify, tier1..4, global, sample, count): launches, ms, msg updates, shots."""
+        pr = _capi.Profile()
+        check(load().bp4m_profile_read(self._h, ctypes.byref(pr)))
+        return {name: {"launches": pr.launches[k], "ms": pr.ms[k], "msg_updates": pr.msg_updates[k],
+                       "shots": pr.shots[k]} for k, name in enumerate(_capi.PROFILE_SLOTS)}
+
     def sample_and_decode(self, shots, seed, iters, opts, first_shot=0, stream_id=0, stream=None):
         c = _capi.Counts()
         check(load().bp4m_sample_and_decode_range(self._h, int(first_shot), int(shots), int(seed),
@@ -139,4 +150,5 @@ class Graph:
                                                   ctypes.byref(c), _stream(stream)))
         return {"shots": c.shots, "fail": list(c.fail), "unconverged": list(c.unconverged),
                 "forced_output": list(c.forced_output), "conv_fail": list(c.conv_fail),
-                "iterations": c.iterations, "msg_updates": c.msg_updates, "defects": c.defects}
+                "iterations": c.iterations, "msg_updates": c.msg_updates, "defects": c.defects,
+                "forced_runs": c.forced_runs, "forced_rounds": c.forced_rounds}

@@ -40,7 +40,8 @@ class Counts(ctypes.Structure):
     _fields_ = [("shots", ctypes.c_uint64), ("fail", ctypes.c_uint64 * 3),
                 ("unconverged", ctypes.c_uint64 * 2), ("forced_output", ctypes.c_uint64 * 2),
                 ("conv_fail", ctypes.c_uint64 * 2), ("iterations", ctypes.c_uint64),
-                ("msg_updates", ctypes.c_uint64), ("defects", ctypes.c_uint64)]
+                ("msg_updates", ctypes.c_uint64), ("defects", ctypes.c_uint64),
+                ("forced_runs", ctypes.c_uint64), ("forced_rounds", ctypes.c_uint64)]
 
 
 class GraphInfo(ctypes.Structure):
@@ -53,6 +54,14 @@ class GraphInfo(ctypes.Structure):
 class Edge(ctypes.Structure):
     _fields_ = [("u", ctypes.c_int32), ("v", ctypes.c_int32), ("obs", ctypes.c_int32),
                 ("pad", ctypes.c_int32), ("q", ctypes.c_double)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 9), ("ms", ctypes.c_double * 9),
+                ("msg_updates", ctypes.c_uint64 * 9), ("shots", ctypes.c_uint64 * 9)]
+
+
+PROFILE_SLOTS = ["classify", "tier1", "tier2", "tier3", "tier4", "tier5", "global", "sample", "count"]
 
 
 class Trace(ctypes.Structure):
@@ -76,6 +85,8 @@ SIGNATURES = {
     "bp4m_sample_and_decode_range": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint64,
                                                     ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(Opts),
                                                     ctypes.POINTER(Counts), _P]),
+    "bp4m_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "bp4m_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "bp4m_free_graph": (None, [_P]),
     "bp4m_last_error": (ctypes.c_char_p, []),
     "bp4m_version": (ctypes.c_char_p, []),

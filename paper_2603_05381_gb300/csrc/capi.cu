@@ -94,11 +94,60 @@ struct bp4m_graph {
     int64_t table_bytes = 0;
     bool prepared[2] = {false, false};
     Workspace ws;
+    // measurement: event pairs around every launch while profiling is on
+    struct ProfEvent {
+        int slot;
+        cudaEvent_t a, b;
+    };
+    bool prof_on = false;
+    std::vector<ProfEvent> prof_events;
+    bp4m_profile_t prof{};
 };
 
 namespace {
 
 int n_words_of(const bp4m_graph* g, int ty) { return (g->host.t[ty].n_det + 31) / 32; }
+
+enum { PROF_CLASSIFY = 0, PROF_GLOBAL = 6, PROF_SAMPLE = 7, PROF_COUNT = 8 };
+
+// Brackets one kernel launch with events when profiling is on.
+struct ProfScope {
+    bp4m_graph* g;
+    int slot;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    ProfScope(bp4m_graph* g_, int slot_, cudaStream_t st_) : g(g_), slot(slot_), st(st_) {
+        if (g->prof_on && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, st);
+    }
+    void end() {
+        if (!a) return;
+        cudaEvent_t b;
+        if (cudaEventCreate(&b) == cudaSuccess) {
+            cudaEventRecord(b, st);
+            g->prof_events.push_back(bp4m_graph::ProfEvent{slot, a, b});
+        } else {
+            cudaEventDestroy(a);
+        }
+        a = nullptr;
+    }
+};
+
+void prof_clear(bp4m_graph* g) {
+    for (auto& e : g->prof_events) {
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    g->prof_events.clear();
+    std::memset(&g->prof, 0, sizeof(g->prof));
+}
+
+void prof_add_counters(bp4m_graph* g, const unsigned long long* c) {
+    if (!g->prof_on) return;
+    for (int t = 0; t < kTiers; ++t) {
+        g->prof.msg_updates[t] += c[C_TIER_MSGS + t];
+        g->prof.shots[t] += c[C_TIER_SHOTS + t];
+    }
+}
 
 DevTables dev_tables(const bp4m_graph* g, int ty) {
     DevTables t;
@@ -249,8 +298,12 @@ int decode_device(bp4m_graph* g, int ty, const uint32_t* synd, int64_t shots, in
     }
     const TierPlan plan = tier_plan(prec);
     CK(cudaMemsetAsync(w.small, 0, (2 * kTiers + 1) * sizeof(int32_t), st));
-    CK(launch_classify(synd, shots, n_words_of(g, ty), plan, w.lists, w.small, w.small + 2 * kTiers,
-                       obs_pred, flags, iters, tr ? tr->defects : nullptr, st));
+    {
+        ProfScope ps(g, PROF_CLASSIFY, st);
+        CK(launch_classify(synd, shots, n_words_of(g, ty), plan, w.lists, w.small, w.small + 2 * kTiers,
+                           obs_pred, flags, iters, tr ? tr->defects : nullptr, st));
+        ps.end();
+    }
     CK(cudaMemcpyAsync(w.host_small, w.small, (2 * kTiers + 1) * sizeof(int32_t),
                        cudaMemcpyDeviceToHost, st));
     CK(cudaEventRecord(w.ev_small, st));
@@ -276,7 +329,10 @@ int decode_device(bp4m_graph* g, int ty, const uint32_t* synd, int64_t shots, in
         a.list = w.lists + (size_t)tier * shots;
         a.count = w.small + tier;
         a.next = w.small + kTiers + tier;
+        a.tier = tier;
+        ProfScope ps(g, tier, st);
         CK(launch_decode_tier(prec, tier, a, g->num_sms, st));
+        ps.end();
     }
     CK(cudaEventSynchronize(w.ev_small));
     const int n_glob = w.host_small[kGlobalTier];
@@ -296,7 +352,10 @@ int decode_device(bp4m_graph* g, int ty, const uint32_t* synd, int64_t shots, in
         a.gscratch = w.gscratch;
         a.gslot_elems = (int64_t)gsmax * gsmax;
         a.gsmax = gsmax;
+        a.tier = kGlobalTier;
+        ProfScope ps(g, PROF_GLOBAL, st);
         CK(launch_decode_global(prec, a, slots, st));
+        ps.end();
     }
     return BP4M_OK;
 }
@@ -316,6 +375,8 @@ void fill_counts(const unsigned long long* c, int n_types, bp4m_counts* out) {
     out->iterations = c[C_ITERS];
     out->msg_updates = c[C_MSGS];
     out->defects = c[C_DEFECTS];
+    out->forced_runs = c[C_FC_RUNS];
+    out->forced_rounds = c[C_FC_ROUNDS];
 }
 
 int sample_into(bp4m_graph* g, uint64_t first_shot, int64_t shots, uint64_t seed, uint32_t sid,
@@ -334,6 +395,7 @@ int sample_into(bp4m_graph* g, uint64_t first_shot, int64_t shots, uint64_t seed
     }
     a.synd = synd_dev;
     a.obs = obs_dev;
+    ProfScope ps(g, PROF_SAMPLE, st);
     if (h.model == BP4M_CIRCUIT) {
         a.thr = g->thr;
         a.uvo = g->uvo;
@@ -343,6 +405,7 @@ int sample_into(bp4m_graph* g, uint64_t first_shot, int64_t shots, uint64_t seed
         for (int k = 0; k < 3; ++k) a.cc_thr[k] = h.cc_thr[k];
         CK(launch_sample_code_capacity(a, st));
     }
+    ps.end();
     return BP4M_OK;
 }
 
@@ -508,10 +571,11 @@ static int decode_common(bp4m_graph* g, const uint32_t* syndromes, int64_t shots
             return fail(BP4M_EINVAL, "trace buffers must be device memory");
         if (shots > kBatch) return fail(BP4M_EINVAL, "traced decodes take at most 2^20 shots");
     }
+    rc = ensure_ws(g, std::max<int64_t>(std::min(kBatch, shots), g->ws.cap));
+    if (rc) return rc;
+    CK(cudaMemsetAsync(g->ws.ctr, 0, C_NUM * sizeof(unsigned long long), st));
     for (int64_t off = 0; off < shots; off += kBatch) {
         const int64_t nb = std::min(kBatch, shots - off);
-        rc = ensure_ws(g, std::max<int64_t>(nb, g->ws.cap));
-        if (rc) return rc;
         Workspace& w = g->ws;
         const uint32_t* sd = syndromes + (size_t)off * nw;
         if (!dev_in) {
@@ -537,6 +601,11 @@ static int decode_common(bp4m_graph* g, const uint32_t* syndromes, int64_t shots
         }
         CK(cudaStreamSynchronize(st));
     }
+    Workspace& w = g->ws;
+    CK(cudaMemcpyAsync(w.host_ctr, w.ctr, C_NUM * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (w.host_ctr[C_ERRORS]) return fail(BP4M_ECUDA, "decoder kernels rejected shots (internal size check)");
+    prof_add_counters(g, w.host_ctr);
     return BP4M_OK;
 }
 
@@ -585,11 +654,14 @@ int bp4m_sample_and_decode_range(bp4m_graph* g, uint64_t first_shot, int64_t sho
             if (rc) return rc;
             woff += n_words_of(g, ty);
         }
+        ProfScope ps(g, PROF_COUNT, st);
         CK(launch_count(w.obs_true, w.obs_pred, w.flags, nb, nt, w.ctr, st));
+        ps.end();
     }
     CK(cudaMemcpyAsync(w.host_ctr, w.ctr, C_NUM * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (w.host_ctr[C_ERRORS]) return fail(BP4M_ECUDA, "decoder kernels rejected shots (internal size check)");
+    prof_add_counters(g, w.host_ctr);
     fill_counts(w.host_ctr, nt, out);
     return BP4M_OK;
 }
@@ -601,8 +673,32 @@ int bp4m_sample_and_decode(bp4m_graph* g, double p, int64_t shots, uint64_t seed
     return bp4m_sample_and_decode_range(g, 0, shots, seed, 0, iters, opts, out, stream);
 }
 
+int bp4m_profile_enable(bp4m_graph* g, int on) {
+    if (!g) return fail(BP4M_EINVAL, "null graph");
+    prof_clear(g);
+    g->prof_on = on != 0;
+    return BP4M_OK;
+}
+
+int bp4m_profile_read(bp4m_graph* g, bp4m_profile_t* out) {
+    if (!g || !out) return fail(BP4M_EINVAL, "null argument");
+    for (auto& e : g->prof_events) {
+        CK(cudaEventSynchronize(e.b));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e.a, e.b));
+        g->prof.ms[e.slot] += ms;
+        g->prof.launches[e.slot] += 1;
+        cudaEventDestroy(e.a);
+        cudaEventDestroy(e.b);
+    }
+    g->prof_events.clear();
+    *out = g->prof;
+    return BP4M_OK;
+}
+
 void bp4m_free_graph(bp4m_graph* g) {
     if (!g) return;
+    if (g->uploaded) prof_clear(g);
     if (g->uploaded) {
         for (int ty = 0; ty < 2; ++ty) {
             cudaFree(g->L32[ty]);

@@ -25,6 +25,10 @@ enum CounterSlot {
     C_CONVFAIL_X, C_CONVFAIL_Z,
     C_ITERS, C_MSGS, C_DEFECTS,
     C_ERRORS,          // shots the kernels refused (internal consistency checks)
+    C_TIER_MSGS,       // 7 slots: message updates per decode tier
+    C_TIER_SHOTS = C_TIER_MSGS + 7,  // 7 slots: shots per decode tier
+    C_FC_RUNS = C_TIER_SHOTS + 7,    // forced-convergence runs
+    C_FC_ROUNDS,                     // locally-dominant rounds summed over runs
     C_NUM
 };
 
@@ -32,11 +36,11 @@ enum CounterSlot {
 enum : uint8_t { F_CONVERGED = 1, F_FORCED_RAN = 2, F_FROM_FORCED = 4 };
 
 // Number of s tiers and the per-tier bookkeeping in the workspace.
-constexpr int kTiers = 6;      // tier 0: s == 0 (done in classify), 1..4 shared memory, 5 global
-constexpr int kGlobalTier = 5;
+constexpr int kTiers = 7;      // tier 0: s == 0 (done in classify), 1..5 shared memory, 6 global
+constexpr int kGlobalTier = 6;
 
 struct TierPlan {
-    int smax[kTiers];  // inclusive upper bound of s for the tier (tier 5: unbounded)
+    int smax[kTiers];  // inclusive upper bound of s for the tier (global tier: unbounded)
 };
 
 struct DecodeArgs {
@@ -51,6 +55,7 @@ struct DecodeArgs {
     int decoder = 0;                 // 0 = BP4M, 1 = BP4MF
     double alpha = 1.0;
     int pitch = 0;                   // shared-memory row pitch in elements
+    int tier = 0;                    // decode tier (per-tier counters)
     // outputs (any may be null)
     uint8_t* obs_pred = nullptr;
     uint8_t* flags = nullptr;
@@ -97,7 +102,7 @@ cudaError_t launch_classify(const uint32_t* synd, int64_t shots, int n_words,
                             int32_t* counts, int32_t* max_s, uint8_t* obs_pred, uint8_t* flags,
                             int16_t* iters, int32_t* tr_defects, cudaStream_t st);
 
-// Launch the decoding kernel of shared-memory tier `tier` (1..4) for precision
+// Launch the decoding kernel of shared-memory tier `tier` (1..5) for precision
 // (0 = FP64, 1 = FP32).  Returns cudaSuccess if the tier is empty by construction.
 cudaError_t launch_decode_tier(int precision, int tier, const DecodeArgs& a, int num_sms,
                                cudaStream_t st);
@@ -106,7 +111,6 @@ cudaError_t launch_decode_global(int precision, const DecodeArgs& a, int slots,
                                  cudaStream_t st);
 // Shared-memory tier plan for a precision.
 TierPlan tier_plan(int precision);
-size_t tier_smem_bytes(int precision, int tier, int* pitch_out);
 cudaError_t prepare_decode_kernels(int precision);
 
 cudaError_t launch_count(const uint8_t* obs_true, const uint8_t* obs_pred, const uint8_t* flags,

@@ -27,6 +27,7 @@
 
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 
 #include "device.cuh"
 
@@ -84,19 +85,80 @@ __device__ __forceinline__ int compact_defects(const uint32_t* __restrict__ sw, 
 }
 
 // Blocks per SM requested from the compiler: enough to keep registers at or below 128.
-constexpr int min_blocks(int nt) { return 65536 / (nt * 128) > 1 ? 65536 / (nt * 128) : 1; }
+__host__ __device__ constexpr int min_blocks(int nt) { return 65536 / (nt * 128) > 1 ? 65536 / (nt * 128) : 1; }
 
-template <typename T, int CH, int G, bool REG_OUT>
-__global__ void __launch_bounds__(CH * G * G, min_blocks(CH * G * G)) decode_smem_kernel(const DecodeArgs a) {
+// Base-2 transcendental helpers of the shared-memory tiers: messages are kept in log2
+// units (every prior is scaled by log2(e) when gathered), so exp and log are single
+// ex2/lg2 operations.
+template <typename T>
+struct B2;
+
+template <>
+struct B2<float> {
+    static __device__ __forceinline__ float ex2(float x) {
+        float y;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    static __device__ __forceinline__ float lg2(float x) {
+        float y;
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    static __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+    static __device__ __forceinline__ float mx(float a, float b) { return fmaxf(a, b); }
+    static __device__ __forceinline__ float mn(float a, float b) { return fminf(a, b); }
+};
+
+template <>
+struct B2<double> {
+    static __device__ __forceinline__ double ex2(double x) { return exp2(x); }
+    static __device__ __forceinline__ double lg2(double x) { return log2(x); }
+    static __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+    static __device__ __forceinline__ double mx(double a, double b) { return fmax(a, b); }
+    static __device__ __forceinline__ double mn(double a, double b) { return fmin(a, b); }
+};
+
+constexpr double kLog2e = 1.4426950408889634074;
+constexpr double kLn2 = 0.69314718055994530942;
+
+// Row pitch in elements.  FP32: pitch = G (mod 32) makes a warp's row reads (R rows x G
+// column groups) hit 32 distinct banks; column accesses are at most 2-way.  FP64: +1.
+template <typename T>
+__host__ __device__ constexpr int pitch_of(int smax, int g) {
+    return sizeof(T) == 8 ? smax + 1 : smax + ((g - smax % 32) % 32 + 32) % 32;
+}
+
+// (max, second max, column of the max) of two partial row scans; ties go to the smaller
+// column.  Commutative, so every thread of a row group ends with the same triple.
+template <typename T>
+__device__ __forceinline__ void combine_max(T& m1, T& m2, int& k, T o1, T o2, int ok) {
+    if (o1 > m1 || (o1 == m1 && ok < k)) {
+        m2 = B2<T>::mx(m1, o2);
+        m1 = o1;
+        k = ok;
+    } else {
+        m2 = B2<T>::mx(m2, o1);
+    }
+}
+
+// Blocks per SM the kernel is compiled for: the 384-thread tier (96 rows, 79 KB of shared
+// memory) runs two blocks per SM; the others are limited by shared memory or 128 registers.
+__host__ __device__ constexpr int blocks_for(int nt) { return nt == 384 ? 2 : min_blocks(nt); }
+
+template <typename T, int CH, int G, bool TRACE>
+__global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G)) decode_smem_kernel(const DecodeArgs a) {
     constexpr int SMAX = CH * G;
     constexpr int NT = SMAX * G;
     constexpr int R = 32 / G;
+    constexpr int P = pitch_of<T>(SMAX, G);
     static_assert(NT % 32 == 0 && NT <= 1024, "block size");
+    using Mask = typename std::conditional<(CH > 32), unsigned long long, unsigned int>::type;
     extern __shared__ __align__(16) unsigned char smem[];
-    const int pitch = a.pitch;
-    T* Mt = reinterpret_cast<T*>(smem);
-    T* Lm = Mt + (size_t)SMAX * pitch;
-    double* rowacc = reinterpret_cast<double*>(Lm + (size_t)SMAX * pitch);
+    T* Mt = reinterpret_cast<T*>(smem);          // Mt[i][k] = M[k][i]; diagonal kept 0
+    T* Lm = Mt + SMAX * P;                          // Lm[i][k] = l_ik in log2 units, -inf past s
+    T* Dg = Lm + SMAX * P;                          // Dg[i] = M[i][i] (factor i to its boundary variable)
+    double* rowacc = reinterpret_cast<double*>(Dg + SMAX + (SMAX & 1));
     int* dets = reinterpret_cast<int*>(rowacc + SMAX);
     int* choice = dets + SMAX;
     short* bestp = reinterpret_cast<short*>(choice + SMAX);
@@ -105,17 +167,22 @@ __global__ void __launch_bounds__(CH * G * G, min_blocks(CH * G * G)) decode_sme
     __shared__ double sh_best_w;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int i = warp * R + (lane % R);
-    const int g = lane / R;
+    const int i = warp * R + (lane % R);   // row (factor) of this thread
+    const int g = lane / R;                // column group: columns k = g + G*c
+    const bool own_diag = (i % G) == g;    // this thread holds column k = i of its row
+    const int c_diag = i / G;
     const int n = a.tb.n_det;
     const T* __restrict__ Ltab = Num<T>::L(a.tb);
     const int count = *a.count;
-    const bool plain = a.alpha == 1.0;
     const T ainv = (T)(1.0 / a.alpha);
     const bool full = (a.decoder == 1) || !a.early_exit;
-    const bool want_w = full;
     T* trl = reinterpret_cast<T*>(a.tr_lambda);
-    unsigned long long acc_it = 0, acc_msg = 0, acc_def = 0;
+    const T ninf = Num<T>::ninf();
+    unsigned long long acc_it = 0, acc_msg = 0, acc_def = 0, acc_shots = 0, acc_fc = 0, acc_fcr = 0;
+
+    T* const row_l = Lm + i * P + g;     // element c at [G*c]
+    T* const row_m = Mt + i * P + g;     // incoming messages M[k][i], element c at [G*c]
+    T* const col_m = Mt + g * P + i;     // own outputs M[i][k] live at Mt[k][i], element c at [G*P*c]
 
     for (;;) {
         if (tid == 0) sh_item = atomicAdd(a.next, 1);
@@ -134,35 +201,40 @@ __global__ void __launch_bounds__(CH * G * G, min_blocks(CH * G * G)) decode_sme
             if (tid == 0 && a.ctr) atomicAdd(a.ctr + C_ERRORS, 1ull);
             continue;
         }
-        const bool tr_on = (trl != nullptr || a.tr_partner != nullptr) && s <= a.s_cap;
+        const bool tr_on = TRACE && s <= a.s_cap;
         if (s == 1) {
             // a single factor with a single variable: the leave-one-out set is empty, the
-            // message is +inf and v_00 is kept at iteration 1
+            // message is +inf and v_00 is kept in every iteration
             if (tid == 0) {
+                const int its = full ? a.T : 1;
                 const int d0 = dets[0];
                 if (a.obs_pred) a.obs_pred[shot] = a.tb.P[(size_t)d0 * n + d0];
                 if (a.flags) a.flags[shot] = F_CONVERGED;
-                if (a.iters) a.iters[shot] = 1;
+                if (a.iters) a.iters[shot] = (int16_t)its;
                 if (tr_on && trl) trl[(size_t)shot * a.s_cap * a.s_cap] = Num<T>::pinf();
                 if (tr_on && a.tr_partner) {
                     a.tr_partner[(size_t)shot * a.s_cap] = 0;
                     for (int k = 1; k < a.s_cap; ++k) a.tr_partner[(size_t)shot * a.s_cap + k] = -1;
                 }
-                acc_it += 1;
-                acc_msg += 1;
+                acc_it += (unsigned long long)its;
+                acc_msg += (unsigned long long)its;
                 acc_def += 1;
+                acc_shots += 1;
             }
             continue;
         }
+        // ---- gather the shot's priors (log2 units); columns past s are -inf so that they
+        // never win a max, add nothing to a sum and are never kept
         for (int r = warp; r < s; r += NT / 32) {
             const T* trow = Ltab + (size_t)dets[r] * n;
-            for (int k = lane; k < s; k += 32) {
-                Lm[r * pitch + k] = __ldg(trow + dets[k]);
-                Mt[r * pitch + k] = T(0);
+            for (int k = lane; k < SMAX; k += 32) {
+                Lm[r * P + k] = k < s ? (T)(__ldg(trow + dets[k]) * (T)kLog2e) : ninf;
+                Mt[r * P + k] = T(0);
             }
         }
         if (tid < SMAX) {
-            matched[tid] = 0;
+            Dg[tid] = T(0);
+            matched[tid] = tid >= s;
             bestp[tid] = -1;
         }
         if (tid == 0) {
@@ -174,37 +246,50 @@ __global__ void __launch_bounds__(CH * G * G, min_blocks(CH * G * G)) decode_sme
         __syncthreads();
 
         const bool act = i < s;
-        const int rowbase = i * pitch;
         T q[CH];
-        T mo[REG_OUT ? CH : 1];
         int t = 0;
         bool any_conv = false, forced_ran = false;
         int out_par = 0, out_forced = 0, out_from_best = 0;
-        int partner = -1;  // the output candidate's partner of row i (g == 0 lanes)
+        int partner = -1;
 
         for (;;) {
-            // ---- read phase: Q for the next update and, for t > 0, lambda^t decisions
-            int cnt = 0, chosen = -1;
+            // ---- read phase: Q = l + M[k][i]/alpha for the next update; for t > 0 the
+            // marginalization of lambda^t = l + (M[i][k] + M[k][i])
+            Mask bits = 0;
+            if (!act) {
 #pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                const int k = g + G * c;
-                T qv = Num<T>::ninf();
-                if (act && k < s) {
-                    const T l = Lm[rowbase + k];
-                    const T x = Mt[rowbase + k];
-                    qv = (k == i) ? l : (plain ? l + x : l + x * ainv);
-                    if (t > 0) {
-                        const T own = REG_OUT ? mo[c] : Mt[k * pitch + i];
-                        const T lam = (k == i) ? l + own : l + (own + x);
-                        if (lam > T(0)) {
-                            ++cnt;
-                            chosen = k;
-                        }
-                        if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + k] = lam;
+                for (int c = 0; c < CH; ++c) q[c] = ninf;
+            } else {
+                if (t == 0) {
+#pragma unroll
+                    for (int c = 0; c < CH; ++c) q[c] = B2<T>::fma_(row_m[G * c], ainv, row_l[G * c]);
+                } else {
+                    Mask b0 = 0, b1 = 0;
+#pragma unroll
+                    for (int c = 0; c < CH; ++c) {
+                        const T l = row_l[G * c];
+                        const T x = row_m[G * c];
+                        const T own = col_m[G * P * c];
+                        q[c] = B2<T>::fma_(x, ainv, l);
+                        const T lam = l + (own + x);
+                        if (c & 1)
+                            b1 |= (Mask)(lam > T(0) ? 1u : 0u) << c;
+                        else
+                            b0 |= (Mask)(lam > T(0) ? 1u : 0u) << c;
+                        if (tr_on && trl && g + G * c < s)
+                            trl[((size_t)shot * a.s_cap + i) * a.s_cap + g + G * c] = lam * (T)kLn2;
+                    }
+                    bits = b0 | b1;
+                    if (own_diag) {
+                        // the boundary variable v_ii: lambda_ii = l_ii + M[i][i]
+                        const T lam = Lm[i * P + i] + Dg[i];
+                        bits = (bits & ~((Mask)1 << c_diag)) | ((Mask)(lam > T(0) ? 1u : 0u) << c_diag);
+                        if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + i] = lam * (T)kLn2;
                     }
                 }
-                q[c] = qv;
             }
+            int cnt = sizeof(Mask) == 8 ? __popcll((unsigned long long)bits) : __popc((unsigned)bits);
+            int chosen = bits ? g + G * ((sizeof(Mask) == 8 ? __ffsll((long long)bits) : __ffs((int)bits)) - 1) : -1;
 #pragma unroll
             for (int off = R; off < 32; off <<= 1) {
                 cnt += __shfl_xor_sync(kFull, cnt, off);
@@ -224,19 +309,18 @@ __global__ void __launch_bounds__(CH * G * G, min_blocks(CH * G * G)) decode_sme
                     forced_ran = true;
                     if (act && g == 0) matched[i] = 0;
                     __syncthreads();
+                    const T lii = act ? Lm[i * P + i] + Dg[i] : ninf;
                     for (int round = 0; round < s; ++round) {
                         const bool open = act && !matched[i];
-                        T bl = Num<T>::ninf();
+                        T bl = ninf;
                         int bk = -1;
                         if (open) {
 #pragma unroll
                             for (int c = 0; c < CH; ++c) {
                                 const int k = g + G * c;
-                                if (k < s && (k == i || !matched[k])) {
-                                    const T l = Lm[rowbase + k];
-                                    const T x = Mt[rowbase + k];
-                                    const T own = REG_OUT ? mo[c] : Mt[k * pitch + i];
-                                    const T lam = (k == i) ? l + own : l + (own + x);
+                                if (k == i || !matched[k]) {
+                                    T lam = row_l[G * c] + (col_m[G * P * c] + row_m[G * c]);
+                                    if (k == i) lam = lii;
                                     if (bk < 0 || lam > bl) {
                                         bl = lam;
                                         bk = k;
@@ -263,8 +347,10 @@ __global__ void __launch_bounds__(CH * G * G, min_blocks(CH * G * G)) decode_sme
                         __syncthreads();
                         if (newm) matched[i] = 1;
                         const int left = __syncthreads_count(open && g == 0 && !newm);
+                        if (tid == 0) acc_fcr += 1;
                         if (left == 0) break;
                     }
+                    if (tid == 0) acc_fc += 1;
                     have_cand = true;
                     cand_forced = true;
                     if (act && g == 0) cand_p = choice[i];
@@ -278,14 +364,13 @@ __global__ void __launch_bounds__(CH * G * G, min_blocks(CH * G * G)) decode_sme
                         if (k >= i) {
                             const size_t off = (size_t)dets[i] * n + dets[k];
                             pc = a.tb.P[off];
-                            if (want_w) w = a.tb.W64[off];
+                            if (full) w = a.tb.W64[off];
                         }
                         rowacc[i] = w;
                     }
                     const int par = __syncthreads_count(pc) & 1;
                     bool finish = false;
                     if (!full) {
-                        // BP4M early exit: first converged iteration, or forced at T
                         out_par = par;
                         out_forced = cand_forced;
                         partner = cand_p;
@@ -304,8 +389,6 @@ __global__ void __launch_bounds__(CH * G * G, min_blocks(CH * G * G)) decode_sme
                                     sh_improve = 1;
                                 }
                             } else {
-                                // BP4M full-T: forced candidate of iteration T against the
-                                // lightest converged one (ties: the converged one)
                                 sh_use_best = sh_best_w <= w;
                             }
                         }
@@ -329,58 +412,66 @@ __global__ void __launch_bounds__(CH * G * G, min_blocks(CH * G * G)) decode_sme
                 }
             }
 
-            // ---- compute phase: leave-one-out max* of every row, written in place
-            T m1 = Num<T>::ninf(), m2 = Num<T>::ninf();
-            int am = 0x7fffffff;
+            // ---- compute phase: leave-one-out max* of every row, in place.  With m1 (at
+            // column am) and m2 the two largest Q of the row and S = sum_k 2^(min(Q_k, m2) - m2)
+            // (the max clamped to m2, so S - 1 = sum_{k != am} 2^(Q_k - m2) >= 1):
+            //   k != am: M'[i][k] = -(m1 + lg2(1 + 2^(m2 - m1) (S - 1 - 2^(Q_k - m2))))
+            //   k == am: M'[i][k] = -(m2 + lg2(S - 1))
+            {
+                T a1 = ninf, a2 = ninf, b1 = ninf, b2 = ninf;
+                int ac = 0x7fffffff, bc = 0x7fffffff;
 #pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                const int k = g + G * c;
-                if (act && k < s) {
+                for (int c = 0; c < CH; c += 2) {
                     const T v = q[c];
-                    if (v > m1) {
-                        m2 = m1;
-                        m1 = v;
-                        am = k;
-                    } else if (v > m2) {
-                        m2 = v;
+                    const bool gt = v > a1;
+                    a2 = B2<T>::mx(a2, B2<T>::mn(v, a1));
+                    a1 = B2<T>::mx(a1, v);
+                    ac = gt ? c : ac;
+                    if (c + 1 < CH) {
+                        const T w = q[c + 1];
+                        const bool gw = w > b1;
+                        b2 = B2<T>::mx(b2, B2<T>::mn(w, b1));
+                        b1 = B2<T>::mx(b1, w);
+                        bc = gw ? c + 1 : bc;
                     }
                 }
-            }
+                // column indices of the two partial maxima (ties to the smaller column)
+                int ka = ac < CH ? g + G * ac : 0x7fffffff;
+                int kb = bc < CH ? g + G * bc : 0x7fffffff;
+                combine_max(a1, a2, ka, b1, b2, kb);
+                T m1 = a1, m2 = a2;
+                int am = ka;
 #pragma unroll
-            for (int off = R; off < 32; off <<= 1) {
-                const T o1 = __shfl_xor_sync(kFull, m1, off);
-                const int oa = __shfl_xor_sync(kFull, am, off);
-                const T o2 = __shfl_xor_sync(kFull, m2, off);
-                if (o1 > m1 || (o1 == m1 && oa < am)) {
-                    m2 = m1 > o2 ? m1 : o2;
-                    m1 = o1;
-                    am = oa;
-                } else {
-                    m2 = m2 > o1 ? m2 : o1;
+                for (int off = R; off < 32; off <<= 1) {
+                    const T o1 = __shfl_xor_sync(kFull, m1, off);
+                    const T o2 = __shfl_xor_sync(kFull, m2, off);
+                    const int ok = __shfl_xor_sync(kFull, am, off);
+                    combine_max(m1, m2, am, o1, o2, ok);
                 }
-            }
-            T S = T(0);
+                T sa = T(0), sb = T(0);
 #pragma unroll
-            for (int c = 0; c < CH; ++c) {
-                const int k = g + G * c;
-                if (act && k < s && k != am) {
-                    const T u = Num<T>::ex(q[c] - m2);
+                for (int c = 0; c < CH; c += 2) {
+                    const T u = B2<T>::ex2(B2<T>::mn(q[c], m2) - m2);
                     q[c] = u;
-                    S += u;
+                    sa += u;
+                    if (c + 1 < CH) {
+                        const T w = B2<T>::ex2(B2<T>::mn(q[c + 1], m2) - m2);
+                        q[c + 1] = w;
+                        sb += w;
+                    }
                 }
-            }
+                T S = sa + sb;
 #pragma unroll
-            for (int off = R; off < 32; off <<= 1) S += __shfl_xor_sync(kFull, S, off);
-            if (act) {
-                const T cf = Num<T>::ex(m2 - m1);
-                const T lS = Num<T>::lg(S);
+                for (int off = R; off < 32; off <<= 1) S += __shfl_xor_sync(kFull, S, off);
+                const T cf = B2<T>::ex2(m2 - m1);
+                const T Aa = B2<T>::fma_(cf, S - T(1), T(1));
+                if (act) {
 #pragma unroll
-                for (int c = 0; c < CH; ++c) {
-                    const int k = g + G * c;
-                    if (k < s) {
-                        const T out = (k == am) ? -(m2 + lS) : -(m1 + Num<T>::lg1p(cf * (S - q[c])));
-                        Mt[k * pitch + i] = out;
-                        if (REG_OUT) mo[c] = out;
+                    for (int c = 0; c < CH; ++c) col_m[G * P * c] = -m1 - B2<T>::lg2(B2<T>::fma_(-cf, q[c], Aa));
+                    if (am % G == g) Mt[am * P + i] = -m2 - B2<T>::lg2(S - T(1));
+                    if (own_diag) {
+                        Dg[i] = Mt[i * P + i];
+                        Mt[i * P + i] = T(0);
                     }
                 }
             }
@@ -405,6 +496,7 @@ __global__ void __launch_bounds__(CH * G * G, min_blocks(CH * G * G)) decode_sme
             acc_it += (unsigned long long)t;
             acc_msg += (unsigned long long)s * s * t;
             acc_def += (unsigned long long)s;
+            acc_shots += 1;
         }
         __syncthreads();
     }
@@ -412,6 +504,10 @@ __global__ void __launch_bounds__(CH * G * G, min_blocks(CH * G * G)) decode_sme
         atomicAdd(a.ctr + C_ITERS, acc_it);
         atomicAdd(a.ctr + C_MSGS, acc_msg);
         atomicAdd(a.ctr + C_DEFECTS, acc_def);
+        atomicAdd(a.ctr + C_TIER_MSGS + a.tier, acc_msg);
+        atomicAdd(a.ctr + C_TIER_SHOTS + a.tier, acc_shots);
+        atomicAdd(a.ctr + C_FC_RUNS, acc_fc);
+        atomicAdd(a.ctr + C_FC_ROUNDS, acc_fcr);
     }
 }
 
@@ -446,7 +542,7 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
     const T ainv = (T)(1.0 / a.alpha);
     const bool full = (a.decoder == 1) || !a.early_exit;
     T* trl = reinterpret_cast<T*>(a.tr_lambda);
-    unsigned long long acc_it = 0, acc_msg = 0, acc_def = 0;
+    unsigned long long acc_it = 0, acc_msg = 0, acc_def = 0, acc_shots = 0, acc_fc = 0, acc_fcr = 0;
 
     for (;;) {
         if (tid == 0) sh_item = atomicAdd(a.next, 1);
@@ -548,8 +644,10 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
                         __syncthreads();
                         for (int r = tid; r < s; r += kGlobThreads)
                             if (!matched[r] && rowacc[r] != 0.0) matched[r] = 1;
+                        if (tid == 0) acc_fcr += 1;
                         if (__syncthreads_count(left) == 0) break;
                     }
+                    if (tid == 0) acc_fc += 1;
                     have_cand = true;
                     cand_forced = true;
                 }
@@ -665,6 +763,7 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
             acc_it += (unsigned long long)t;
             acc_msg += (unsigned long long)s * s * t;
             acc_def += (unsigned long long)s;
+            acc_shots += 1;
         }
         __syncthreads();
     }
@@ -672,6 +771,10 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
         atomicAdd(a.ctr + C_ITERS, acc_it);
         atomicAdd(a.ctr + C_MSGS, acc_msg);
         atomicAdd(a.ctr + C_DEFECTS, acc_def);
+        atomicAdd(a.ctr + C_TIER_MSGS + a.tier, acc_msg);
+        atomicAdd(a.ctr + C_TIER_SHOTS + a.tier, acc_shots);
+        atomicAdd(a.ctr + C_FC_RUNS, acc_fc);
+        atomicAdd(a.ctr + C_FC_ROUNDS, acc_fcr);
     }
 }
 
@@ -680,45 +783,40 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
 struct TierCfg {
     int smax;
     int ch, g;
-    bool reg_out;
 };
 
-// FP32: 32/64/128/160 rows in shared memory; FP64: 32/64/112.
-constexpr TierCfg kCfg32[5] = {{0, 0, 0, false}, {32, 32, 1, true}, {64, 32, 2, true},
-                               {128, 32, 4, true}, {160, 40, 4, false}};
-constexpr TierCfg kCfg64[5] = {{0, 0, 0, false}, {32, 16, 2, false}, {64, 16, 4, false},
-                               {112, 14, 8, false}, {112, 14, 8, false}};
+// FP32: 32/64/96/128/160 rows in shared memory; FP64: 32/64/112 (tiers 4, 5 unused).
+constexpr TierCfg kCfg32[6] = {{0, 0, 0}, {32, 32, 1}, {64, 32, 2}, {96, 24, 4}, {128, 32, 4}, {160, 40, 4}};
+constexpr TierCfg kCfg64[6] = {{0, 0, 0}, {32, 16, 2}, {64, 16, 4}, {112, 28, 4}, {112, 28, 4}, {112, 28, 4}};
 
-int pitch_for(int smax, int g) {
-    int p = smax;
-    while (p % 32 != g % 32) ++p;
-    return p;
-}
-
-template <typename T, int CH, int G, bool REG>
-size_t smem_bytes_of(int* pitch) {
+template <typename T, int CH, int G>
+size_t smem_bytes_of() {
     constexpr int SMAX = CH * G;
-    const int p = pitch_for(SMAX, G);
-    if (pitch) *pitch = p;
-    return (size_t)2 * SMAX * p * sizeof(T) + (size_t)SMAX * (sizeof(double) + 2 * sizeof(int) +
-                                                              sizeof(short) + 1) + 16;
+    constexpr int P = pitch_of<T>(SMAX, G);
+    return (size_t)(2 * SMAX * P + SMAX + (SMAX & 1)) * sizeof(T) +
+           (size_t)SMAX * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 16;
 }
 
-template <typename T, int CH, int G, bool REG>
-cudaError_t run_tier(const DecodeArgs& a0, int num_sms, cudaStream_t st, bool prepare_only) {
-    int pitch = 0;
-    const size_t smem = smem_bytes_of<T, CH, G, REG>(&pitch);
-    auto kern = decode_smem_kernel<T, CH, G, REG>;
+template <typename T, int CH, int G, bool TRACE>
+cudaError_t run_tier(const DecodeArgs& a, int num_sms, cudaStream_t st, bool prepare_only) {
+    const size_t smem = smem_bytes_of<T, CH, G>();
+    auto kern = decode_smem_kernel<T, CH, G, TRACE>;
     if (prepare_only)
         return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CH * G * G, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    DecodeArgs a = a0;
-    a.pitch = pitch;
     kern<<<per_sm * num_sms, CH * G * G, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <typename T, int CH, int G>
+cudaError_t run_tier2(const DecodeArgs& a, int num_sms, cudaStream_t st, bool prep, bool trace) {
+    cudaError_t e = run_tier<T, CH, G, false>(a, num_sms, st, prep);
+    if (prep && e == cudaSuccess) return run_tier<T, CH, G, true>(a, num_sms, st, prep);
+    if (prep || !trace) return e;
+    return run_tier<T, CH, G, true>(a, num_sms, st, prep);
 }
 
 template <typename T>
@@ -726,22 +824,44 @@ cudaError_t dispatch_tier(int tier, const DecodeArgs& a, int num_sms, cudaStream
 
 template <>
 cudaError_t dispatch_tier<float>(int tier, const DecodeArgs& a, int num_sms, cudaStream_t st, bool prep) {
+    const bool tr = a.tr_lambda != nullptr || a.tr_partner != nullptr;
+    if (!prep && tr) {
+        switch (tier) {
+            case 1: return run_tier<float, 32, 1, true>(a, num_sms, st, false);
+            case 2: return run_tier<float, 32, 2, true>(a, num_sms, st, false);
+            case 3: return run_tier<float, 24, 4, true>(a, num_sms, st, false);
+            case 4: return run_tier<float, 32, 4, true>(a, num_sms, st, false);
+            case 5: return run_tier<float, 40, 4, true>(a, num_sms, st, false);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (tier) {
-        case 1: return run_tier<float, 32, 1, true>(a, num_sms, st, prep);
-        case 2: return run_tier<float, 32, 2, true>(a, num_sms, st, prep);
-        case 3: return run_tier<float, 32, 4, true>(a, num_sms, st, prep);
-        case 4: return run_tier<float, 40, 4, false>(a, num_sms, st, prep);
+        case 1: return run_tier2<float, 32, 1>(a, num_sms, st, prep, false);
+        case 2: return run_tier2<float, 32, 2>(a, num_sms, st, prep, false);
+        case 3: return run_tier2<float, 24, 4>(a, num_sms, st, prep, false);
+        case 4: return run_tier2<float, 32, 4>(a, num_sms, st, prep, false);
+        case 5: return run_tier2<float, 40, 4>(a, num_sms, st, prep, false);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <>
 cudaError_t dispatch_tier<double>(int tier, const DecodeArgs& a, int num_sms, cudaStream_t st, bool prep) {
+    const bool tr = a.tr_lambda != nullptr || a.tr_partner != nullptr;
+    if (!prep && tr) {
+        switch (tier) {
+            case 1: return run_tier<double, 16, 2, true>(a, num_sms, st, false);
+            case 2: return run_tier<double, 16, 4, true>(a, num_sms, st, false);
+            case 3: return run_tier<double, 28, 4, true>(a, num_sms, st, false);
+            case 4: case 5: return cudaSuccess;  // same bound as tier 3: never populated
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (tier) {
-        case 1: return run_tier<double, 16, 2, false>(a, num_sms, st, prep);
-        case 2: return run_tier<double, 16, 4, false>(a, num_sms, st, prep);
-        case 3: return run_tier<double, 14, 8, false>(a, num_sms, st, prep);
-        case 4: return cudaSuccess;  // same bound as tier 3: never populated
+        case 1: return run_tier2<double, 16, 2>(a, num_sms, st, prep, false);
+        case 2: return run_tier2<double, 16, 4>(a, num_sms, st, prep, false);
+        case 3: return run_tier2<double, 28, 4>(a, num_sms, st, prep, false);
+        case 4: case 5: return cudaSuccess;
         default: return cudaErrorInvalidValue;
     }
 }
@@ -751,32 +871,14 @@ cudaError_t dispatch_tier<double>(int tier, const DecodeArgs& a, int num_sms, cu
 TierPlan tier_plan(int precision) {
     TierPlan p{};
     const TierCfg* c = precision == 0 ? kCfg64 : kCfg32;
-    for (int k = 0; k < kTiers; ++k) p.smax[k] = k < 5 ? c[k].smax : 0x7fffffff;
+    for (int k = 0; k < kGlobalTier; ++k) p.smax[k] = c[k].smax;
     p.smax[kGlobalTier] = 0x7fffffff;
     return p;
 }
 
-size_t tier_smem_bytes(int precision, int tier, int* pitch_out) {
-    if (precision == 0) {
-        switch (tier) {
-            case 1: return smem_bytes_of<double, 16, 2, false>(pitch_out);
-            case 2: return smem_bytes_of<double, 16, 4, false>(pitch_out);
-            case 3: case 4: return smem_bytes_of<double, 14, 8, false>(pitch_out);
-        }
-    } else {
-        switch (tier) {
-            case 1: return smem_bytes_of<float, 32, 1, true>(pitch_out);
-            case 2: return smem_bytes_of<float, 32, 2, true>(pitch_out);
-            case 3: return smem_bytes_of<float, 32, 4, true>(pitch_out);
-            case 4: return smem_bytes_of<float, 40, 4, false>(pitch_out);
-        }
-    }
-    return 0;
-}
-
 cudaError_t prepare_decode_kernels(int precision) {
     DecodeArgs dummy;
-    for (int tier = 1; tier <= 4; ++tier) {
+    for (int tier = 1; tier < kGlobalTier; ++tier) {
         cudaError_t e = precision == 0 ? dispatch_tier<double>(tier, dummy, 0, 0, true)
                                        : dispatch_tier<float>(tier, dummy, 0, 0, true);
         if (e != cudaSuccess) return e;

@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances.  Sampling, syndromes and observable flips are bit-exact.  Decoding is compared
+per shot on (predicted flip, converged flag, iterations, output source, matching): it must
+agree exactly unless the oracle's decision margin on that shot is below tau, the smallest
+|lambda| (or gap between two posteriors ordered by forced convergence) the oracle met; a
+shot with a smaller margin may legitimately flip under a different rounding.  tau is 1e-9
+for FP64 messages and 1e-2 for FP32 (FP32 posteriors carry an absolute error of a few 1e-5
+after tens of iterations on lambdas of magnitude up to ~100, see the lambda test).
+"""
+import numpy as np
+import pytest
+
+import paper_2603_05381_gb300 as pkg
+from gpu_util import compare_shots, gpu_decode, gpu_sample, oracle_partner, torch_cuda
+from oracle.bp import run_bp
+from oracle.circuit import Noise, circuit_graph
+from oracle.decoders import decode_shot
+from oracle.graph import circuit_tables, code_capacity_tables
+from oracle.sampler import code_capacity_sample, graph_sample, pack_syndromes, unpack_syndromes
+from oracle.surface import code_capacity_graph, rotated_code
+
+pytestmark = pytest.mark.gpu
+
+TAU64 = 1e-9
+TAU32 = 1e-2
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return torch_cuda()
+
+
+_cache = {}
+
+
+def circuit_pair(d, p):
+    key = ("c", d, p)
+    if key not in _cache:
+        og, _, _ = circuit_graph(d, Noise(p))
+        _cache[key] = (pkg.Graph(d, "circuit", p), og, circuit_tables(og))
+    return _cache[key]
+
+
+def as_bool(synd_dev, n_det):
+    return unpack_syndromes(synd_dev.cpu().numpy().view(np.uint32), n_det)
+
+
+# ------------------------------------------------------------------ sampler
+
+
+@pytest.mark.parametrize("d,p,first,n", [(3, 0.01, 0, 3000), (5, 0.005, 123456789, 3000), (7, 0.003, 2**33, 1000)])
+def test_sampler_circuit_bit_exact(torch, d, p, first, n):
+    g, og, _ = circuit_pair(d, p)
+    (synd,), obs = gpu_sample(g, first, n, seed=0xDEADBEEF12345, stream_id=3)
+    osyn, oobs = graph_sample(og, np.arange(first, first + n, dtype=np.uint64), seed=0xDEADBEEF12345, stream=3)
+    assert np.array_equal(as_bool(synd, og.n_det), osyn)
+    assert np.array_equal(obs[0].cpu().numpy(), oobs)
+
+
+@pytest.mark.parametrize("d,p", [(3, 0.05), (5, 0.1), (9, 0.15), (21, 0.12)])
+def test_sampler_code_capacity_bit_exact(torch, d, p):
+    g = pkg.Graph(d, "code_capacity", p)
+    n = 2000
+    synds, obs = gpu_sample(g, 77, n, seed=1)
+    code = rotated_code(d)
+    ref = code_capacity_sample(code, p, np.arange(77, 77 + n), seed=1)
+    for ty, kind in ((0, "X"), (1, "Z")):
+        n_det = g.info()["n_det"][ty]
+        assert np.array_equal(as_bool(synds[ty], n_det), ref[kind][0])
+        assert np.array_equal(obs[ty].cpu().numpy(), ref[kind][1])
+
+
+def test_sampler_d13_full_batch_sampled_rows(torch):
+    # the benchmark's launch: 2^20 shots of the d = 13, p = 0.005 circuit in one batch
+    g, og, _ = circuit_pair(13, 0.005)
+    n = 1 << 20
+    (synd,), obs = gpu_sample(g, 0, n, seed=1)
+    rng = np.random.default_rng(2)
+    rows = np.sort(rng.choice(n, size=400, replace=False))
+    got = unpack_syndromes(synd[torch.as_tensor(rows, device="cuda")].cpu().numpy().view(np.uint32), og.n_det)
+    osyn, oobs = graph_sample(og, rows.astype(np.uint64), seed=1)
+    assert np.array_equal(got, osyn)
+    assert np.array_equal(obs[0].cpu().numpy()[rows], oobs)
+    s = synd.cpu().numpy().view(np.uint32)
+    counts = np.unpackbits(s.view(np.uint8), axis=1).sum(axis=1)
+    # mean defect count against the sum of per-detector firing probabilities
+    prod = np.ones(og.n_det)
+    for (u, v, _, q) in og.edges:
+        prod[u] *= 1 - 2 * q
+        if v < og.n_det:
+            prod[v] *= 1 - 2 * q
+    pr = (1 - prod) / 2
+    sd = np.sqrt((pr * (1 - pr)).sum() / n)
+    assert abs(counts.mean() - pr.sum()) < 5 * sd
+
+
+# ------------------------------------------------------------------ decoding, FP64
+
+
+def test_fp64_code_capacity_d3_config(torch):
+    # rotated d = 3, p = 0.05, 10^4 shots from seed 1, FP64 messages, 50 iterations with
+    # early exit, X and Z decoded separately
+    d, p, n, T = 3, 0.05, 10000, 50
+    g = pkg.Graph(d, "code_capacity", p)
+    synds, obs = gpu_sample(g, 0, n, seed=1)
+    code = rotated_code(d)
+    opts_base = dict(precision="fp64", early_exit=True)
+    fails = {}
+    unconv = {}
+    for ty, kind in ((0, "X"), (1, "Z")):
+        tb = code_capacity_tables(code_capacity_graph(code, kind), p)
+        opts = pkg.make_opts(type=ty, **opts_base)
+        res = gpu_decode(g, synds[ty], T, opts, s_cap=8)
+        assert np.array_equal(res["obs"], res["obs2"])
+        sb = as_bool(synds[ty], tb.n_det)
+        cnt, bad = compare_shots(tb, sb, res, T, range(n), TAU64)
+        assert all(m < TAU64 for _, m in bad), bad[:5]
+        assert len(bad) <= 2
+        fails[ty] = res["obs"] != obs[ty].cpu().numpy()
+        unconv[ty] = int((res["flags"] & 1 == 0).sum())
+    counts = g.sample_and_decode(n, seed=1, iters=T, opts=pkg.make_opts(**opts_base))
+    assert counts["shots"] == n
+    assert counts["fail"][0] == int(fails[0].sum())
+    assert counts["fail"][1] == int(fails[1].sum())
+    assert counts["fail"][2] == int((fails[0] | fails[1]).sum())
+    assert counts["unconverged"] == [unconv[0], unconv[1]]
+
+
+@pytest.mark.parametrize("decoder,early,alpha", [("bp4m", True, 1.0), ("bp4m", False, 1.0),
+                                                 ("bp4mf", False, 1.0), ("bp4mf", False, 0.85)])
+def test_fp64_circuit_d5_decoders(torch, decoder, early, alpha):
+    g, og, ot = circuit_pair(5, 0.008)
+    n, T = 300, 30
+    (synd,), _ = gpu_sample(g, 0, n, seed=11)
+    opts = pkg.make_opts(precision="fp64", early_exit=early, decoder=decoder, alpha=alpha)
+    res = gpu_decode(g, synd, T, opts, s_cap=64)
+    sb = as_bool(synd, og.n_det)
+    cnt, bad = compare_shots(ot, sb, res, T, range(n), TAU64, decoder=decoder, early_exit=early, alpha=alpha)
+    assert all(m < TAU64 for _, m in bad), bad[:5]
+    assert len(bad) <= 2
+
+
+# ------------------------------------------------------------------ decoding, FP32
+
+
+@pytest.mark.parametrize("decoder,early,alpha", [("bp4m", True, 1.0), ("bp4m", False, 1.0),
+                                                 ("bp4mf", False, 1.0), ("bp4mf", False, 0.85)])
+def test_fp32_circuit_d5_decoders(torch, decoder, early, alpha):
+    g, og, ot = circuit_pair(5, 0.008)
+    n, T = 400, 30
+    (synd,), _ = gpu_sample(g, 1000, n, seed=5)
+    opts = pkg.make_opts(precision="fp32", early_exit=early, decoder=decoder, alpha=alpha)
+    res = gpu_decode(g, synd, T, opts, s_cap=64)
+    sb = as_bool(synd, og.n_det)
+    cnt, bad = compare_shots(ot, sb, res, T, range(n), TAU32, decoder=decoder, early_exit=early, alpha=alpha)
+    print("fp32 d5 %s early=%s alpha=%g: %d/%d shots differ, margins %s" % (
+        decoder, early, alpha, len(bad), cnt, [round(m, 6) for _, m in bad[:8]]))
+    assert all(m < TAU32 for _, m in bad), bad[:5]
+    assert len(bad) <= cnt // 50
+
+
+@pytest.mark.parametrize("prec,rtol", [("fp64", 1e-10), ("fp32", 1e-4)])
+def test_posterior_llrs_match(torch, prec, rtol):
+    # lambda after exactly T iterations (full-T mode runs all of them)
+    g, og, ot = circuit_pair(5, 0.008)
+    n = 48
+    (synd,), _ = gpu_sample(g, 5000, n, seed=9)
+    sb = as_bool(synd, og.n_det)
+    worst = 0.0
+    for T in (1, 2, 5, 12):
+        opts = pkg.make_opts(precision=prec, early_exit=False)
+        res = gpu_decode(g, synd, T, opts, s_cap=64)
+        for k in range(n):
+            dets = np.flatnonzero(sb[k])
+            s = len(dets)
+            if s < 2:
+                continue
+            L = ot.L[np.ix_(dets, dets)]
+            lam = run_bp(L, T)[-1][1]
+            got = res["lam"][k][:s, :s].astype(np.float64)
+            scale = np.abs(L) + 1.0
+            err = np.max(np.abs(got - lam) / scale)
+            worst = max(worst, err)
+    print("%s: worst |dlambda|/(|l|+1) = %.3g" % (prec, worst))
+    assert worst < rtol
+
+
+# ------------------------------------------------------------------ tiers and edge cases
+
+
+def _random_syndromes(n_det, sizes, seed):
+    rng = np.random.default_rng(seed)
+    rows = np.zeros((len(sizes), n_det), dtype=bool)
+    for r, s in enumerate(sizes):
+        rows[r, rng.choice(n_det, size=s, replace=False)] = True
+    return rows
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+@pytest.mark.parametrize("early", [True, False])
+def test_every_tier_boundary_d13(torch, prec, early):
+    # defect counts on both sides of every shared-memory tier bound and in the global tier
+    g, og, ot = circuit_pair(13, 0.005)
+    sizes = [0, 1, 2, 3, 31, 32, 33, 63, 64, 65, 111, 112, 113, 127, 128, 129, 159, 160, 161, 200]
+    sb = _random_syndromes(og.n_det, sizes, seed=17 + early)
+    synd = torch.as_tensor(pack_syndromes(sb).view(np.int32), device="cuda")
+    T = 6
+    opts = pkg.make_opts(precision=prec, early_exit=early)
+    res = gpu_decode(g, synd, T, opts, s_cap=208)
+    assert list(res["s"]) == sizes
+    tau = TAU64 if prec == "fp64" else TAU32
+    cnt, bad = compare_shots(ot, sb, res, T, range(len(sizes)), tau, early_exit=early)
+    assert all(m < tau for _, m in bad), bad
+    assert res["obs"][0] == 0 and res["iters"][0] == 0 and res["flags"][0] & 1
+    assert res["iters"][1] == (1 if early else T) and res["partner"][1][0] == 0
+
+
+def test_host_buffers_match_device_buffers(torch):
+    g, og, ot = circuit_pair(5, 0.008)
+    n, T = 2000, 20
+    (synd,), _ = gpu_sample(g, 0, n, seed=3)
+    opts = pkg.make_opts(precision="fp32")
+    host_in = synd.cpu().numpy()
+    a = np.zeros(n, np.uint8)
+    b = np.zeros(n, np.uint8)
+    c = np.zeros(n, np.int16)
+    g.decode_batch(host_in, T, opts, a, b, c)
+    res = gpu_decode(g, synd, T, opts)
+    assert np.array_equal(a, res["obs2"]) and np.array_equal(b, res["conv"]) and np.array_equal(c, res["iters"])
+    # an empty call is a no-op
+    g.decode_batch(host_in[:0], T, opts, a[:0], b[:0], c[:0])
+
+
+def test_bench_workload_d13_sampled_shots(torch):
+    # the benchmark's launch configuration: 2^20 shots of d = 13, p = 0.005, FP32,
+    # 50 iterations with early exit, decoded in one batch; sampled shots against the oracle
+    g, og, ot = circuit_pair(13, 0.005)
+    n, T = 1 << 20, 50
+    (synd,), obs = gpu_sample(g, 0, n, seed=1)
+    opts = pkg.make_opts(precision="fp32", early_exit=True)
+    torch_ = torch
+    pred = torch_.empty((n,), dtype=torch_.uint8, device="cuda")
+    conv = torch_.empty((n,), dtype=torch_.uint8, device="cuda")
+    its = torch_.empty((n,), dtype=torch_.int16, device="cuda")
+    g.decode_batch(synd, T, opts, pred, conv, its)
+    torch_.cuda.synchronize()
+    rng = np.random.default_rng(4)
+    rows = np.sort(rng.choice(n, size=14, replace=False))
+    sub = synd[torch_.as_tensor(rows, device="cuda")].contiguous()
+    res = gpu_decode(g, sub, T, opts, s_cap=200)
+    assert np.array_equal(res["obs"], pred.cpu().numpy()[rows])
+    assert np.array_equal(res["iters"], its.cpu().numpy()[rows])
+    sb = as_bool(sub, og.n_det)
+    cnt, bad = compare_shots(ot, sb, res, T, range(len(rows)), TAU32)
+    print("d13 sampled: %d/%d differ %s" % (len(bad), cnt, bad))
+    assert all(m < TAU32 for _, m in bad), bad
+    # the fused sample-and-decode path counts exactly what the per-shot outputs give
+    counts = g.sample_and_decode(n, seed=1, iters=T, opts=opts)
+    fails = int((pred.cpu().numpy() != obs[0].cpu().numpy()).sum())
+    assert counts["shots"] == n and counts["fail"][0] == fails
+    assert counts["unconverged"][0] == int((conv.cpu().numpy() == 0).sum())
+    assert counts["iterations"] == int(its.cpu().numpy().astype(np.int64).sum())
