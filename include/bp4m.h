@@ -177,6 +177,33 @@ int bp4m_sample_and_decode_range(bp4m_graph* g, uint64_t first_shot, int64_t sho
                                  uint64_t seed, uint32_t stream_id, int iters,
                                  const bp4m_opts* opts, bp4m_counts* out, void* stream);
 
+/* Decoding without any device allocation.  The paper has no counterpart: this entry point
+   exists for callers that cannot call cudaMalloc, such as a decoding service that must
+   keep a fixed device-memory footprint after start-up, or code running where an
+   allocation would synchronise the device or is not permitted.  Every other decoding
+   entry point allocates its workspace on first use; this one allocates nothing.
+
+   Decodes `shots` bit-packed syndromes of one type exactly like bp4m_decode_batch with the
+   same opts, but every shot goes through the library's global-memory decoding kernel, whose
+   scratch is a file-scope device array of fixed size (16 slots of 192 x 192 x 3 FP64
+   values, 14.2 MB) that every GPU loading the library holds until the process exits.
+   Arguments: `syndromes` uint32 [shots][n_words], `obs_pred`, `converged` (0/1) and
+   `iters_used` per shot: all DEVICE memory of the current device (outputs may be NULL).
+   Preconditions and limits:
+     - the graph's tables must already be on this device: any other decoding call on the
+       graph (for example one bp4m_decode_batch) uploads them during set-up;
+     - the first call on a device looks up the device address of the scratch array
+       (cudaGetSymbolAddress); make that first call before any stream capture;
+     - a shot with more than 192 unsatisfied detectors is rejected: the call returns
+       BP4M_EINVAL and that shot's outputs are 0;
+     - every call shares the one array, which keeps the last call's contents: calls that
+       overlap on the GPU (other streams, other threads) race and must be serialised by
+       the caller.
+   Synchronises `stream`. */
+int bp4m_decode_noalloc(const bp4m_graph* g, const uint32_t* syndromes, int64_t shots, int iters,
+                        const bp4m_opts* opts, uint8_t* obs_pred, uint8_t* converged,
+                        int16_t* iters_used, void* stream);
+
 /* Kernel timing for measurement.  While enabled, every kernel the library launches for
    this graph is bracketed by CUDA events recorded on the launch stream, and the
    algorithmic message updates of each decoding tier are counted.  Enabling resets the

@@ -673,6 +673,48 @@ int bp4m_sample_and_decode(bp4m_graph* g, double p, int64_t shots, uint64_t seed
     return bp4m_sample_and_decode_range(g, 0, shots, seed, 0, iters, opts, out, stream);
 }
 
+int bp4m_decode_noalloc(const bp4m_graph* g, const uint32_t* syndromes, int64_t shots, int iters,
+                        const bp4m_opts* opts, uint8_t* obs_pred, uint8_t* converged,
+                        int16_t* iters_used, void* stream) {
+    // No allocation on any path of this function: it reads the graph's resident tables
+    // and uses the library's static scratch array (see launch_decode_noalloc).
+    if (!g || !syndromes) return fail(BP4M_EINVAL, "null argument");
+    if (shots < 0 || shots > 0x7fffffff) return fail(BP4M_EINVAL, "shots out of range");
+    int rc = check_opts(g, opts, iters);
+    if (rc) return rc;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (!g->uploaded || g->device != dev)
+        return fail(BP4M_EINVAL, "the graph's tables are not on this device: run one bp4m_decode_batch on it "
+                                 "during set-up first");
+    if (!is_device_ptr(syndromes) || (obs_pred && !is_device_ptr(obs_pred)) ||
+        (converged && !is_device_ptr(converged)) || (iters_used && !is_device_ptr(iters_used)))
+        return fail(BP4M_EINVAL, "bp4m_decode_noalloc takes device buffers only");
+    if (shots == 0) return BP4M_OK;
+    const int ty = g->host.n_types == 2 ? opts->type : 0;
+    DecodeArgs a;
+    a.tb = dev_tables(g, ty);
+    a.synd = syndromes;
+    a.shots = shots;
+    a.T = iters;
+    a.early_exit = opts->early_exit ? 1 : 0;
+    a.decoder = opts->decoder;
+    a.alpha = opts->alpha;
+    a.obs_pred = obs_pred;
+    a.flags = converged;
+    a.flags_mode = 1;
+    a.iters = iters_used;
+    a.ctr = nullptr;
+    int too_many = 0;
+    cudaError_t e = launch_decode_noalloc(opts->precision == BP4M_FP64 ? 0 : 1, a, shots,
+                                          static_cast<cudaStream_t>(stream), &too_many);
+    if (too_many)
+        return fail(BP4M_EINVAL, "a shot has more than " + std::to_string(noalloc_max_defects()) +
+                                     " unsatisfied detectors, the limit of bp4m_decode_noalloc");
+    if (e != cudaSuccess) return cuda_fail(e, "bp4m_decode_noalloc");
+    return BP4M_OK;
+}
+
 int bp4m_profile_enable(bp4m_graph* g, int on) {
     if (!g) return fail(BP4M_EINVAL, "null graph");
     prof_clear(g);

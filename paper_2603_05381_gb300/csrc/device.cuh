@@ -66,6 +66,10 @@ struct DecodeArgs {
     int16_t* tr_partner = nullptr;
     int32_t* tr_defects = nullptr;
     int s_cap = 0;
+    // shot source when `list`/`count` are null: shots 0 .. count_val-1 in order
+    int64_t count_val = 0;
+    int* err_flag = nullptr;         // set to 1 by a block that meets a shot it cannot hold
+    int flags_mode = 0;              // 0: `flags` gets F_* bits; 1: `flags` gets converged 0/1
     // global tier: scratch slots
     void* gscratch = nullptr;
     int64_t gslot_elems = 0;         // elements per slot for each of the three matrices
@@ -112,6 +116,13 @@ cudaError_t launch_decode_global(int precision, const DecodeArgs& a, int slots,
 // Shared-memory tier plan for a precision.
 TierPlan tier_plan(int precision);
 cudaError_t prepare_decode_kernels(int precision);
+
+// Decodes shots 0 .. shots-1 with the global-memory kernel using the library's file-scope
+// device scratch array instead of allocated memory (see bp4m_decode_noalloc).  Returns
+// cudaErrorInvalidValue with *too_many set when a shot exceeds the array's defect limit.
+cudaError_t launch_decode_noalloc(int precision, DecodeArgs a, int64_t shots, cudaStream_t st,
+                                  int* too_many);
+int noalloc_max_defects();
 
 cudaError_t launch_count(const uint8_t* obs_true, const uint8_t* obs_pred, const uint8_t* flags,
                          int64_t shots, int n_types, unsigned long long* ctr, cudaStream_t st);

@@ -28,6 +28,7 @@
 #include <cfloat>
 #include <cmath>
 #include <type_traits>
+#include <atomic>
 
 #include "device.cuh"
 
@@ -537,7 +538,7 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = a.tb.n_det;
     const T* __restrict__ Ltab = Num<T>::L(a.tb);
-    const int count = *a.count;
+    const int64_t count = a.count ? (int64_t)*a.count : a.count_val;
     const bool plain = a.alpha == 1.0;
     const T ainv = (T)(1.0 / a.alpha);
     const bool full = (a.decoder == 1) || !a.early_exit;
@@ -549,7 +550,7 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
         __syncthreads();
         const int item = sh_item;
         if (item >= count) break;
-        const int64_t shot = a.list[item];
+        const int64_t shot = a.list ? (int64_t)a.list[item] : (int64_t)item;
         if (warp == 0) {
             const int s0 = compact_defects(a.synd + (size_t)shot * a.tb.n_words, a.tb.n_words,
                                            dets, gsmax, lane);
@@ -557,8 +558,29 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
         }
         __syncthreads();
         const int s = sh_s;
-        if (s > gsmax || s < 2) {
-            if (tid == 0 && a.ctr) atomicAdd(a.ctr + C_ERRORS, 1ull);
+        if (s > gsmax) {
+            if (tid == 0) {
+                if (a.ctr) atomicAdd(a.ctr + C_ERRORS, 1ull);
+                if (a.err_flag) atomicOr(a.err_flag, 1);
+                if (a.obs_pred) a.obs_pred[shot] = 0;
+                if (a.flags) a.flags[shot] = 0;
+                if (a.iters) a.iters[shot] = 0;
+            }
+            continue;
+        }
+        if (s < 2) {
+            // no defect: nothing to match; one defect: it goes to the boundary in every
+            // iteration (empty leave-one-out set)
+            if (tid == 0) {
+                const int its = s == 0 ? 0 : (full ? a.T : 1);
+                if (a.obs_pred) a.obs_pred[shot] = s == 0 ? 0 : a.tb.P[(size_t)dets[0] * n + dets[0]];
+                if (a.flags) a.flags[shot] = a.flags_mode ? 1 : F_CONVERGED;
+                if (a.iters) a.iters[shot] = (int16_t)its;
+                acc_it += (unsigned long long)its;
+                acc_msg += (unsigned long long)(s * its);
+                acc_def += (unsigned long long)s;
+                acc_shots += 1;
+            }
             continue;
         }
         const bool tr_on = (trl != nullptr || a.tr_partner != nullptr) && s <= a.s_cap;
@@ -757,8 +779,9 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
         if (tid == 0) {
             if (a.obs_pred) a.obs_pred[shot] = (uint8_t)out_par;
             if (a.flags)
-                a.flags[shot] = (uint8_t)((any_conv ? F_CONVERGED : 0) | (forced_ran ? F_FORCED_RAN : 0) |
-                                          (out_forced ? F_FROM_FORCED : 0));
+                a.flags[shot] = a.flags_mode ? (uint8_t)(any_conv ? 1 : 0)
+                                             : (uint8_t)((any_conv ? F_CONVERGED : 0) | (forced_ran ? F_FORCED_RAN : 0) |
+                                                         (out_forced ? F_FROM_FORCED : 0));
             if (a.iters) a.iters[shot] = (int16_t)t;
             acc_it += (unsigned long long)t;
             acc_msg += (unsigned long long)s * s * t;
@@ -777,6 +800,23 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
         atomicAdd(a.ctr + C_FC_ROUNDS, acc_fcr);
     }
 }
+
+// ------------------------------------------------------------------ no-allocation scratch
+//
+// bp4m_decode_noalloc serves callers that cannot allocate device memory.  Its scratch is
+// this file-scope array: a 256-byte header (work counter, error flag) and 16 slots of
+// three 192 x 192 FP64 matrices, 14.2 MB held by every GPU that loads the library until the
+// process exits.  Host code must not use the array's name as a device address; the
+// address is looked up once per device with cudaGetSymbolAddress and cached.
+constexpr int kNoAllocMaxDefects = 192;
+constexpr int kNoAllocSlots = 16;
+constexpr size_t kNoAllocHeader = 256;
+constexpr size_t kNoAllocSlotElems = (size_t)kNoAllocMaxDefects * kNoAllocMaxDefects;
+constexpr size_t kNoAllocBytes = kNoAllocHeader + (size_t)kNoAllocSlots * 3 * kNoAllocSlotElems * sizeof(double);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kMaxDevices = 64;
+std::atomic<void*> g_noalloc_addr[kMaxDevices];
 
 // ------------------------------------------------------------------ tier table
 
@@ -890,6 +930,54 @@ cudaError_t launch_decode_tier(int precision, int tier, const DecodeArgs& a, int
                                cudaStream_t st) {
     return precision == 0 ? dispatch_tier<double>(tier, a, num_sms, st, false)
                           : dispatch_tier<float>(tier, a, num_sms, st, false);
+}
+
+int noalloc_max_defects() { return kNoAllocMaxDefects; }
+
+cudaError_t launch_decode_noalloc(int precision, DecodeArgs a, int64_t shots, cudaStream_t st,
+                                  int* too_many) {
+    *too_many = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    void* base = g_noalloc_addr[dev].load();
+    if (!base) {
+        // set-up, once per device with that device current: the device address of the array
+        e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev].store(base);
+    }
+    unsigned char* b = static_cast<unsigned char*>(base);
+    // the header (work counter and error flag) must start at zero; the matrices are
+    // initialised per shot by the kernel
+    e = cudaMemsetAsync(b, 0, kNoAllocHeader, st);
+    if (e != cudaSuccess) return e;
+    a.list = nullptr;
+    a.count = nullptr;
+    a.count_val = shots;
+    a.next = reinterpret_cast<int32_t*>(b);
+    a.err_flag = reinterpret_cast<int*>(b) + 1;
+    a.gscratch = b + kNoAllocHeader;
+    a.gslot_elems = (int64_t)kNoAllocSlotElems;
+    a.gsmax = kNoAllocMaxDefects;
+    const size_t smem = (size_t)a.gsmax * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 16;
+    if (precision == 0)
+        decode_global_kernel<double><<<kNoAllocSlots, kGlobThreads, smem, st>>>(a);
+    else
+        decode_global_kernel<float><<<kNoAllocSlots, kGlobThreads, smem, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int flag = 0;
+    e = cudaMemcpyAsync(&flag, a.err_flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    if (flag) {
+        *too_many = 1;
+        return cudaErrorInvalidValue;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_decode_global(int precision, const DecodeArgs& a, int slots, cudaStream_t st) {
