@@ -39,8 +39,8 @@ extern "C" {
 #define BP4M_ECUDA        -5   /* a CUDA runtime call failed (message has the CUDA error) */
 
 /* ---- code, noise and decoder descriptions ---- */
-#define BP4M_ROTATED   0
-#define BP4M_UNROTATED 1       /* reserved: BP4M_EUNSUPPORTED */
+#define BP4M_ROTATED   0       /* d^2 data qubits, weight-2 boundary plaquettes */
+#define BP4M_UNROTATED 1       /* d^2 + (d-1)^2 data qubits on a (2d-1) x (2d-1) grid */
 
 #define BP4M_MEMORY_Z  0
 
@@ -50,10 +50,10 @@ extern "C" {
 #define BP4M_PRIOR_P     0     /* code capacity prior (p/(1-p))^w with the printed p */
 #define BP4M_PRIOR_2P3   1     /* code capacity prior with the X (or Z) marginal 2p/3 */
 
-/* Code: rotated surface code of distance d.  rounds = 0 with BP4M_CODE_CAPACITY;
+/* Code: surface code of distance d.  rounds = 0 with BP4M_CODE_CAPACITY;
    with BP4M_CIRCUIT rounds = 0 means d rounds (Sec. "Numerical Results": R = d). */
 typedef struct {
-    int family;   /* BP4M_ROTATED */
+    int family;   /* BP4M_ROTATED or BP4M_UNROTATED */
     int d;        /* odd distance >= 3 */
     int rounds;   /* syndrome-extraction rounds (circuit only) */
     int basis;    /* BP4M_MEMORY_Z */

@@ -1,5 +1,5 @@
-"""Rotated memory-Z circuit and its detector error model by backward Pauli-frame
-propagation (oracle side).
+"""Memory-Z circuits (rotated and unrotated surface code) and their detector error model by
+backward Pauli-frame propagation (oracle side).
 
 Test infrastructure only: nothing in the product path imports this module.
 
@@ -15,15 +15,15 @@ Circuit (qubits: data r*d+c, then X-ancillas, then Z-ancillas in check order):
   round 1..d:
     DEP1(p) on data
     H on X-ancillas; DEP1(p) on X-ancillas; DEP1(p) on idle qubits
-    four CNOT layers; X-check corners in the order NW, SW, NE, SE (ancilla controls),
-      Z-check corners in the order NW, NE, SW, SE (data controls);
+    four CNOT layers in the code's schedule (see surface.py), ancilla controls for
+      X-checks and data controls for Z-checks;
       after each layer DEP2(p) on every CNOT pair and DEP1(p) on the idle qubits
     H on X-ancillas; DEP1(p) on X-ancillas; DEP1(p) on idle qubits
     X-flip(p) on ancillas; measure-and-reset ancillas; X-flip(p) on ancillas
   X-flip(p) on data; measure data
 Z-detectors: round 1 outcome; rounds 2..d outcome XOR previous outcome; a final layer
 comparing each Z-check's data parity with its last outcome.  Numbered by
-(round, pr, pc) ascending, the final layer being round d+1.  Observable: parity of the
+(round, check row, check column) ascending, the final layer being round d+1.  Observable: parity of the
 data outcomes on supp(Z_L).  X-detectors (rounds 2..d) exist only for the determinism
 check: the Z-part of the model never needs them.
 
@@ -34,10 +34,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .surface import rotated_code
-
-_LAYER_X = [(0, 0), (1, 0), (0, 1), (1, 1)]  # NW, SW, NE, SE as (dr, dc) from the plaquette corner
-_LAYER_Z = [(0, 0), (0, 1), (1, 0), (1, 1)]  # NW, NE, SW, SE
+from .surface import make_code
 
 
 @dataclass
@@ -62,9 +59,9 @@ class Circuit:
     zdet_coords: list = field(default_factory=list)  # (round, pr, pc)
 
 
-def memory_z_circuit(d, noise):
-    code = rotated_code(d)
-    n = d * d
+def memory_z_circuit(d, noise, family="rotated"):
+    code = make_code(d, family)
+    n = code.n
     nx, nz = len(code.x_checks), len(code.z_checks)
     xanc = [n + a for a in range(nx)]
     zanc = [n + nx + a for a in range(nz)]
@@ -81,16 +78,14 @@ def memory_z_circuit(d, noise):
     layers = []
     for k in range(4):
         pairs = []
-        for a, (pr, pc, _) in enumerate(code.x_checks):
-            dr, dc = _LAYER_X[k]
-            r, c = pr + dr, pc + dc
-            if 0 <= r < d and 0 <= c < d:
-                pairs.append((xanc[a], r * d + c))
-        for a, (pr, pc, _) in enumerate(code.z_checks):
-            dr, dc = _LAYER_Z[k]
-            r, c = pr + dr, pc + dc
-            if 0 <= r < d and 0 <= c < d:
-                pairs.append((r * d + c, zanc[a]))
+        for a in range(nx):
+            q = code.x_sched[a][k]
+            if q is not None:
+                pairs.append((xanc[a], q))
+        for a in range(nz):
+            q = code.z_sched[a][k]
+            if q is not None:
+                pairs.append((q, zanc[a]))
         layers.append(pairs)
 
     ops.append(("R", allq, 0.0))
@@ -245,7 +240,7 @@ def merge_probabilities(qs):
     return acc
 
 
-def circuit_graph(d, noise):
+def circuit_graph(d, noise, family="rotated"):
     """Z-part detector graph of the rotated memory-Z experiment.
 
     Every mechanism is reduced to its Z-detector set and observable bit; mechanisms with
@@ -254,7 +249,7 @@ def circuit_graph(d, noise):
     `decompose_hyperedge`).  Returns (DetGraph-like dict, stats).
     """
     from .surface import DetGraph
-    circ = memory_z_circuit(d, noise)
+    circ = memory_z_circuit(d, noise, family)
     fr = backward_frames(circ)
     nz = fr.n_zdet
     groups = {}

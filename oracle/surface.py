@@ -1,8 +1,9 @@
-"""Rotated surface code geometry and its code-capacity decoding graphs (oracle side).
+"""Surface code geometry (rotated and unrotated) and code-capacity decoding graphs
+(oracle side).
 
 Test infrastructure only: nothing in the product path imports this module.
 
-Layout (one fixed convention, shared as an interface with the product):
+Rotated layout (one fixed convention, shared as an interface with the product):
   * data qubit (r, c), r, c in [0, d), index r*d + c;
   * a plaquette is named by its north-west corner (pr, pc), pr, pc in [-1, d-1], and
     covers the data qubits (pr, pc), (pr, pc+1), (pr+1, pc), (pr+1, pc+1) that exist;
@@ -10,6 +11,15 @@ Layout (one fixed convention, shared as an interface with the product):
   * all four-qubit plaquettes are kept; two-qubit plaquettes are kept on the top and
     bottom edges when they are Z-type and on the left and right edges when X-type;
   * Z_L is Z on column c = 0 and X_L is X on row r = 0.
+
+Unrotated layout: a (2d-1) x (2d-1) grid; data qubits at (r, c) with r + c even, numbered
+row-major; Z-checks at (r odd, c even) and X-checks at (r even, c odd), each acting on its
+N, S, W, E neighbours inside the grid; Z_L is Z on row 0 of the data, X_L is X on column 0.
+
+CNOT schedules (the order in which a check's ancilla meets its data qubits; None = no
+qubit in that step):
+  rotated:   X-checks NW, SW, NE, SE; Z-checks NW, NE, SW, SE;
+  unrotated: X-checks N, W, E, S;     Z-checks N, E, W, S.
 
 The paper (Sec. "MWPM on the surface code") decodes X and Z errors separately on the
 decoding graph of the matching checks.  "Type X" below means X errors detected by the
@@ -22,16 +32,19 @@ import numpy as np
 
 
 @dataclass
-class RotatedCode:
+class SurfaceCode:
     d: int
-    z_checks: list  # [(pr, pc, [qubits])] sorted by (pr, pc)
+    z_checks: list  # [(row, col, [qubits])] sorted by (row, col)
     x_checks: list
     zl: list        # qubits in supp(Z_L)
     xl: list        # qubits in supp(X_L)
+    n: int = 0
+    z_sched: list = None  # per Z-check: 4 qubits (or None) in CNOT order
+    x_sched: list = None
+    family: str = "rotated"
 
-    @property
-    def n(self):
-        return self.d * self.d
+
+RotatedCode = SurfaceCode
 
 
 def rotated_code(d):
@@ -54,7 +67,51 @@ def rotated_code(d):
                 (z_checks if kind == "Z" else x_checks).append((pr, pc, qs))
     zl = [r * d + 0 for r in range(d)]
     xl = [0 * d + c for c in range(d)]
-    return RotatedCode(d, z_checks, x_checks, zl, xl)
+
+    def sched(checks, order):
+        out = []
+        for pr, pc, _ in checks:
+            row = []
+            for dr, dc in order:
+                r, c = pr + dr, pc + dc
+                row.append(r * d + c if 0 <= r < d and 0 <= c < d else None)
+            out.append(row)
+        return out
+
+    nw, sw, ne, se = (0, 0), (1, 0), (0, 1), (1, 1)
+    return SurfaceCode(d, z_checks, x_checks, zl, xl, d * d,
+                       sched(z_checks, [nw, ne, sw, se]), sched(x_checks, [nw, sw, ne, se]), "rotated")
+
+
+def unrotated_code(d):
+    if d < 2:
+        raise ValueError("distance must be at least 2")
+    L = 2 * d - 1
+    index = {}
+    for r in range(L):
+        for c in range(L):
+            if (r + c) % 2 == 0:
+                index[(r, c)] = len(index)
+    z_checks, x_checks = [], []
+    for r in range(L):
+        for c in range(L):
+            if (r + c) % 2 == 1:
+                qs = [index[(r + dr, c + dc)] for dr, dc in ((-1, 0), (0, -1), (0, 1), (1, 0))
+                      if (r + dr, c + dc) in index]
+                (z_checks if r % 2 == 1 else x_checks).append((r, c, sorted(qs)))
+    zl = [index[(0, c)] for c in range(0, L, 2)]
+    xl = [index[(r, 0)] for r in range(0, L, 2)]
+    N, S, W, E = (-1, 0), (1, 0), (0, -1), (0, 1)
+
+    def sched(checks, order):
+        return [[index.get((r + dr, c + dc)) for dr, dc in order] for r, c, _ in checks]
+
+    return SurfaceCode(d, z_checks, x_checks, zl, xl, len(index),
+                       sched(z_checks, [N, E, W, S]), sched(x_checks, [N, W, E, S]), "unrotated")
+
+
+def make_code(d, family="rotated"):
+    return rotated_code(d) if family == "rotated" else unrotated_code(d)
 
 
 def parity_check_matrices(code):

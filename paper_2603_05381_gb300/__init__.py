@@ -60,10 +60,12 @@ def make_opts(precision=FP32, early_exit=True, decoder="bp4m", alpha=1.0, type=0
 class Graph:
     """A static detector graph with its per-pair tables (bp4m_build_graph)."""
 
-    def __init__(self, d, model="circuit", p=0.005, rounds=0, prior="p", pair_through_boundary=False):
+    def __init__(self, d, model="circuit", p=0.005, rounds=0, prior="p", pair_through_boundary=False,
+                 family="rotated"):
         lib = load()
         m = {"code_capacity": CODE_CAPACITY, "circuit": CIRCUIT}[model] if isinstance(model, str) else model
-        code = _capi.Code(_capi.ROTATED, int(d), int(rounds), _capi.MEMORY_Z)
+        fam = {"rotated": _capi.ROTATED, "unrotated": _capi.UNROTATED}[family]
+        code = _capi.Code(fam, int(d), int(rounds), _capi.MEMORY_Z)
         noise = _capi.Noise(m, float(p), {"p": PRIOR_P, "2p/3": PRIOR_2P3}[prior],
                             1 if pair_through_boundary else 0)
         h = ctypes.c_void_p()

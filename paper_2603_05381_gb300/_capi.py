@@ -9,6 +9,7 @@ BP4M_OK = 0
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "EUNSUPPORTED", -4: "ETIMEOUT", -5: "ECUDA"}
 
 ROTATED = 0
+UNROTATED = 1
 MEMORY_Z = 0
 CODE_CAPACITY = 0
 CIRCUIT = 1

@@ -4,7 +4,7 @@
 // has a node per check of the matching type and an edge per data qubit between its one
 // or two checks (one check: an edge to the boundary).
 //
-// Circuit level (Sec. "Numerical Results"): the rotated memory-Z circuit with d rounds,
+// Circuit level (Sec. "Numerical Results"): the memory-Z circuit with d rounds,
 // depolarizing noise of strength p after every gate, on the data before every round and on
 // idle qubits of every gate layer, and flips of probability p after resets and before
 // measurements.  Every non-identity Pauli of a channel is an independent mechanism.  Its
@@ -39,40 +39,95 @@ namespace {
 
 constexpr double kInf = std::numeric_limits<double>::infinity();
 
-struct Plaquette {
-    int pr, pc;
-    std::vector<int> qubits;  // data qubits r*d+c
+struct Check {
+    int row, col;               // position (rotated: north-west corner of the plaquette)
+    std::vector<int> qubits;    // data qubits, ascending
+    int sched[4];               // data qubit met in each CNOT step, -1 for none
 };
 
-// Plaquette (pr, pc) covers data (pr..pr+1, pc..pc+1); X-type iff pr+pc is even.  Kept:
-// every weight-4 plaquette; weight-2 ones on the top/bottom edges if Z-type and on the
-// left/right edges if X-type.  Z_L = column 0, X_L = row 0.
-void rotated_plaquettes(int d, std::vector<Plaquette>& xs, std::vector<Plaquette>& zs) {
-    xs.clear();
-    zs.clear();
+struct CodeLayout {
+    int n = 0;                  // data qubits
+    std::vector<Check> xs, zs;  // X- and Z-checks in (row, col) order
+    std::vector<char> in_zl;    // data qubit in supp(Z_L)
+    std::vector<char> in_xl;    // data qubit in supp(X_L)
+};
+
+// Rotated code.  Data (r, c) in [0, d)^2, index r*d + c.  Plaquette (pr, pc) covers data
+// (pr..pr+1, pc..pc+1); X-type iff pr+pc is even.  Kept: every weight-4 plaquette;
+// weight-2 ones on the top/bottom edges if Z-type and on the left/right edges if X-type.
+// Z_L = column 0, X_L = row 0.  CNOT order: X-checks NW, SW, NE, SE; Z-checks NW, NE,
+// SW, SE.
+CodeLayout rotated_layout(int d) {
+    CodeLayout L;
+    L.n = d * d;
+    const int xo[4][2] = {{0, 0}, {1, 0}, {0, 1}, {1, 1}};
+    const int zo[4][2] = {{0, 0}, {0, 1}, {1, 0}, {1, 1}};
+    auto at = [d](int r, int c) { return (r >= 0 && r < d && c >= 0 && c < d) ? r * d + c : -1; };
     for (int pr = -1; pr < d; ++pr) {
         for (int pc = -1; pc < d; ++pc) {
-            Plaquette pq{pr, pc, {}};
+            Check ch{pr, pc, {}, {-1, -1, -1, -1}};
             for (int dr = 0; dr < 2; ++dr)
                 for (int dc = 0; dc < 2; ++dc) {
-                    int r = pr + dr, c = pc + dc;
-                    if (r >= 0 && r < d && c >= 0 && c < d) pq.qubits.push_back(r * d + c);
+                    const int q = at(pr + dr, pc + dc);
+                    if (q >= 0) ch.qubits.push_back(q);
                 }
-            bool x_type = (((pr + pc) % 2) + 2) % 2 == 0;
+            const bool x_type = (((pr + pc) % 2) + 2) % 2 == 0;
             bool keep;
-            if (pq.qubits.size() == 4) {
+            if (ch.qubits.size() == 4) {
                 keep = true;
-            } else if (pq.qubits.size() == 2) {
-                bool top_bottom = (pr == -1 || pr == d - 1);
+            } else if (ch.qubits.size() == 2) {
+                const bool top_bottom = (pr == -1 || pr == d - 1);
                 keep = top_bottom ? !x_type : x_type;
             } else {
                 keep = false;
             }
             if (!keep) continue;
-            (x_type ? xs : zs).push_back(pq);
+            const int(*o)[2] = x_type ? xo : zo;
+            for (int k = 0; k < 4; ++k) ch.sched[k] = at(pr + o[k][0], pc + o[k][1]);
+            std::sort(ch.qubits.begin(), ch.qubits.end());
+            (x_type ? L.xs : L.zs).push_back(ch);
         }
     }
-    // generated in (pr, pc) ascending order already
+    L.in_zl.assign(L.n, 0);
+    L.in_xl.assign(L.n, 0);
+    for (int r = 0; r < d; ++r) L.in_zl[r * d] = 1;
+    for (int c = 0; c < d; ++c) L.in_xl[c] = 1;
+    return L;
+}
+
+// Unrotated code.  A (2d-1) x (2d-1) grid; data at (r, c) with r + c even, numbered
+// row-major; Z-checks at (r odd, c even), X-checks at (r even, c odd), each acting on its
+// N, S, W, E neighbours.  Z_L = data row 0, X_L = data column 0.  CNOT order: X-checks
+// N, W, E, S; Z-checks N, E, W, S.
+CodeLayout unrotated_layout(int d) {
+    CodeLayout L;
+    const int G = 2 * d - 1;
+    std::vector<int> index(G * G, -1);
+    for (int r = 0; r < G; ++r)
+        for (int c = 0; c < G; ++c)
+            if ((r + c) % 2 == 0) index[r * G + c] = L.n++;
+    auto at = [&](int r, int c) { return (r >= 0 && r < G && c >= 0 && c < G) ? index[r * G + c] : -1; };
+    const int N[2] = {-1, 0}, S[2] = {1, 0}, W[2] = {0, -1}, E[2] = {0, 1};
+    const int* xo[4] = {N, W, E, S};
+    const int* zo[4] = {N, E, W, S};
+    for (int r = 0; r < G; ++r)
+        for (int c = 0; c < G; ++c) {
+            if ((r + c) % 2 == 0) continue;
+            const bool z_type = r % 2 == 1;
+            Check ch{r, c, {}, {-1, -1, -1, -1}};
+            const int* const* o = z_type ? zo : xo;
+            for (int k = 0; k < 4; ++k) {
+                ch.sched[k] = at(r + o[k][0], c + o[k][1]);
+                if (ch.sched[k] >= 0) ch.qubits.push_back(ch.sched[k]);
+            }
+            std::sort(ch.qubits.begin(), ch.qubits.end());
+            (z_type ? L.zs : L.xs).push_back(ch);
+        }
+    L.in_zl.assign(L.n, 0);
+    L.in_xl.assign(L.n, 0);
+    for (int c = 0; c < G; c += 2) L.in_zl[at(0, c)] = 1;
+    for (int r = 0; r < G; r += 2) L.in_xl[at(r, 0)] = 1;
+    return L;
 }
 
 // ---------------------------------------------------------------- circuit model
@@ -95,10 +150,9 @@ struct Circuit {
     std::vector<int> obs;
 };
 
-Circuit memory_z(int d, double p) {
-    std::vector<Plaquette> xs, zs;
-    rotated_plaquettes(d, xs, zs);
-    const int n = d * d, nx = (int)xs.size(), nz = (int)zs.size();
+Circuit memory_z(const CodeLayout& lay, int d, double p) {
+    const int n = lay.n, nx = (int)lay.xs.size(), nz = (int)lay.zs.size();
+    const std::vector<Check>& zs = lay.zs;
     Circuit c;
     c.nq = n + nx + nz;
     std::vector<int> data(n), xa(nx), za(nz), anc, all(c.nq);
@@ -111,26 +165,24 @@ Circuit memory_z(int d, double p) {
     std::vector<int> idle_h = data;
     idle_h.insert(idle_h.end(), za.begin(), za.end());
 
-    // CNOT layers: X-checks visit NW, SW, NE, SE (ancilla controls), Z-checks visit
-    // NW, NE, SW, SE (data controls).
-    const int xo[4][2] = {{0, 0}, {1, 0}, {0, 1}, {1, 1}};
-    const int zo[4][2] = {{0, 0}, {0, 1}, {1, 0}, {1, 1}};
+    // CNOT layers in the checks' schedule: the ancilla controls for X-checks, the data
+    // qubit controls for Z-checks.
     std::vector<Op> cx_layers(4);
     std::vector<std::vector<int>> idle_cx(4);
     for (int k = 0; k < 4; ++k) {
         Op op{OpK::Cnot, {}, {}, 0.0, 0};
         std::vector<char> busy(c.nq, 0);
         for (int a = 0; a < nx; ++a) {
-            int r = xs[a].pr + xo[k][0], cc = xs[a].pc + xo[k][1];
-            if (r >= 0 && r < d && cc >= 0 && cc < d) {
+            const int q = lay.xs[a].sched[k];
+            if (q >= 0) {
                 op.a.push_back(xa[a]);
-                op.b.push_back(r * d + cc);
+                op.b.push_back(q);
             }
         }
         for (int a = 0; a < nz; ++a) {
-            int r = zs[a].pr + zo[k][0], cc = zs[a].pc + zo[k][1];
-            if (r >= 0 && r < d && cc >= 0 && cc < d) {
-                op.a.push_back(r * d + cc);
+            const int q = zs[a].sched[k];
+            if (q >= 0) {
+                op.a.push_back(q);
                 op.b.push_back(za[a]);
             }
         }
@@ -188,7 +240,8 @@ Circuit memory_z(int d, double p) {
         for (int q : zs[a].qubits) det.push_back(drec + q);
         c.zdet.push_back(det);
     }
-    for (int r = 0; r < d; ++r) c.obs.push_back(drec + r * d + 0);
+    for (int q = 0; q < n; ++q)
+        if (lay.in_zl[q]) c.obs.push_back(drec + q);
     return c;
 }
 
@@ -397,9 +450,9 @@ void all_pairs(int n_det, const std::vector<std::vector<Arc>>& adj, bool through
 
 int build_host_graph(const bp4m_code& code, const bp4m_noise& noise, HostGraph& g,
                      std::string& err) {
-    if (code.family != BP4M_ROTATED) {
-        err = "only the rotated surface code is implemented";
-        return BP4M_EUNSUPPORTED;
+    if (code.family != BP4M_ROTATED && code.family != BP4M_UNROTATED) {
+        err = "unknown code family";
+        return BP4M_EINVAL;
     }
     if (code.basis != BP4M_MEMORY_Z) {
         err = "only the memory-Z experiment is implemented";
@@ -423,8 +476,8 @@ int build_host_graph(const bp4m_code& code, const bp4m_noise& noise, HostGraph& 
     g.p = noise.p;
     g.prior_conv = noise.prior_conv;
     g.through_boundary = noise.pair_through_boundary ? 1 : 0;
-    std::vector<Plaquette> xs, zs;
-    rotated_plaquettes(d, xs, zs);
+    const CodeLayout lay = code.family == BP4M_ROTATED ? rotated_layout(d) : unrotated_layout(d);
+    g.family = code.family;
 
     if (noise.model == BP4M_CODE_CAPACITY) {
         if (code.rounds != 0) {
@@ -433,23 +486,24 @@ int build_host_graph(const bp4m_code& code, const bp4m_noise& noise, HostGraph& 
         }
         g.rounds = 0;
         g.n_types = 2;
-        g.n_units = d * d;
+        g.n_units = lay.n;
         for (int k = 1; k <= 3; ++k)
             g.cc_thr[k - 1] = (uint32_t)std::floor((double)k * noise.p / 3.0 * 4294967296.0);
         const double pp = noise.prior_conv == BP4M_PRIOR_P ? noise.p : 2.0 * noise.p / 3.0;
         const double c = std::log((1.0 - pp) / pp);
         for (int ty = 0; ty < 2; ++ty) {
-            // type 0: X errors on Z-checks, obs = column 0;  type 1: Z errors on X-checks, obs = row 0
-            const std::vector<Plaquette>& chk = ty == 0 ? zs : xs;
+            // type 0: X errors on the Z-checks, obs = qubit in supp(Z_L);
+            // type 1: Z errors on the X-checks, obs = qubit in supp(X_L)
+            const std::vector<Check>& chk = ty == 0 ? lay.zs : lay.xs;
             TypeTables& t = g.t[ty];
             t.n_det = (int)chk.size();
-            std::vector<std::vector<int>> touch(d * d);
+            std::vector<std::vector<int>> touch(lay.n);
             for (int a = 0; a < t.n_det; ++a)
                 for (int q : chk[a].qubits) touch[q].push_back(a);
-            g.cc_u[ty].resize(d * d);
-            g.cc_v[ty].resize(d * d);
-            g.cc_obs[ty].resize(d * d);
-            for (int q = 0; q < d * d; ++q) {
+            g.cc_u[ty].resize(lay.n);
+            g.cc_v[ty].resize(lay.n);
+            g.cc_obs[ty].resize(lay.n);
+            for (int q = 0; q < lay.n; ++q) {
                 std::vector<int> ts = touch[q];
                 std::sort(ts.begin(), ts.end());
                 int u, v;
@@ -463,7 +517,7 @@ int build_host_graph(const bp4m_code& code, const bp4m_noise& noise, HostGraph& 
                     err = "geometry error: a qubit touches 0 or >2 checks of one type";
                     return BP4M_EINVAL;
                 }
-                int obs = ty == 0 ? (q % d == 0) : (q / d == 0);
+                const int obs = ty == 0 ? lay.in_zl[q] : lay.in_xl[q];
                 g.cc_u[ty][q] = u;
                 g.cc_v[ty][q] = v;
                 g.cc_obs[ty][q] = (uint8_t)obs;
@@ -485,7 +539,7 @@ int build_host_graph(const bp4m_code& code, const bp4m_noise& noise, HostGraph& 
     }
     g.rounds = d;
     g.n_types = 1;
-    Circuit c = memory_z(d, noise.p);
+    Circuit c = memory_z(lay, d, noise.p);
     std::vector<Fault> faults = enumerate_faults(c);
     std::vector<Effect> eff = simulate_faults(c, faults);
     const int n_det = (int)c.zdet.size();

@@ -28,6 +28,7 @@ struct TypeTables {
 
 struct HostGraph {
     int model = 0;
+    int family = 0;
     int d = 0;
     int rounds = 0;
     double p = 0.0;

@@ -94,3 +94,22 @@ def test_circuit_graph_d13_matches_oracle(lib):
     for i in srcs:
         assert np.array_equal(Wg[i, i:], W[i, i:])
         assert np.array_equal(Pg[i, i:], P[i, i:])
+
+
+@pytest.mark.parametrize("d", [3, 5, 7])
+def test_unrotated_tables_match_oracle(lib, d):
+    from paper_2603_05381_gb300 import Graph
+    from oracle.surface import unrotated_code
+    g = Graph(d, "circuit", 0.006, family="unrotated")
+    og, _, _ = circuit_graph(d, Noise(0.006), "unrotated")
+    ot = circuit_tables(og)
+    assert g.export("edges") == list(og.edges)
+    assert np.array_equal(g.export("W"), ot.W) and np.array_equal(g.export("parity"), ot.P)
+    np.testing.assert_allclose(g.export("L"), ot.L, rtol=1e-15, atol=0)
+    g2 = Graph(d, "code_capacity", 0.07, family="unrotated")
+    assert g2.info()["n_units"] == d * d + (d - 1) ** 2
+    for ty, kind in ((0, "X"), (1, "Z")):
+        cg = code_capacity_graph(unrotated_code(d), kind)
+        ct = code_capacity_tables(cg, 0.07)
+        assert [(u, v, o) for (u, v, o, _) in g2.export("edges", ty)] == [(u, v, o) for (u, v, o, _) in cg.edges]
+        assert np.array_equal(g2.export("W", ty), ct.W) and np.array_equal(g2.export("parity", ty), ct.P)

@@ -106,3 +106,45 @@ def test_merge_is_odd_parity_probability():
             brute += pr
     assert merge_probabilities(qs) == pytest.approx(brute, rel=1e-14)
     assert merge_probabilities([0.25]) == 0.25
+
+
+def test_unrotated_state_vector_d2():
+    # the unrotated schedule (X: N, W, E, S; Z: N, E, W, S) on the d = 2 code (9 qubits):
+    # noiseless detectors are 0 and injected Paulis flip what the error model says
+    circ = memory_z_circuit(2, Noise(0.0), "unrotated")
+    for seed in range(4):
+        z, x, obs = detector_values(circ, run_circuit(circ, np.random.default_rng(seed)))
+        assert not any(z) and not any(x) and obs == 0
+    circ = memory_z_circuit(2, Noise(0.01), "unrotated")
+    fr = backward_frames(circ)
+    locs = _locations(circ)
+    assert len(locs) == len(fr.mechanisms)
+    rng = np.random.default_rng(8)
+    for m in rng.choice(len(locs), size=80, replace=False):
+        z, _, obs = detector_values(circ, run_circuit(circ, np.random.default_rng(int(m)), inject=locs[m]))
+        zs, ob, _ = fr.mechanisms[m]
+        assert tuple(np.flatnonzero(z)) == zs and obs == ob
+
+
+@pytest.mark.parametrize("d", [3, 5, 7])
+def test_unrotated_dem_structure_and_distance(d):
+    g, circ, st = circuit_graph(d, Noise(0.004), "unrotated")
+    assert g.n_det == d * (d - 1) * (d + 1)
+    assert st["nondeterministic"] == [] and st["hyperedges"] == 0
+    fr = backward_frames(circ, include_x_detectors=True)
+    assert fr.nondeterministic == set()
+    if d <= 5:
+        assert _odd_cycle_through_boundary(g) == d
+
+
+def test_unrotated_reduces_to_code_capacity_graph():
+    from oracle.surface import code_capacity_graph, unrotated_code
+    d, p = 3, 0.01
+    noise = Noise(p, data_round=True, gates=False, idle=False, reset_flip=False, meas_flip=False)
+    g, _, _ = circuit_graph(d, noise, "unrotated")
+    cc = code_capacity_graph(unrotated_code(d), "X")
+    want = set()
+    for rnd in range(d):
+        for (u, v, ob, _) in cc.edges:
+            want.add((u + rnd * cc.n_det, g.n_det if v == cc.n_det else v + rnd * cc.n_det, ob))
+    assert {(u, v, ob) for (u, v, ob, _) in g.edges} == want

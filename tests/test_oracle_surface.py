@@ -105,3 +105,25 @@ def test_graph_distance_equals_d(d, kind):
     assert g.n_det == (d * d - 1) // 2
     assert len(g.edges) == d * d
     assert _odd_cycle_through_boundary(g) == d
+
+
+@pytest.mark.parametrize("d", [2, 3, 5, 7])
+def test_unrotated_counts_commutation_distance(d):
+    from oracle.surface import unrotated_code
+    code = unrotated_code(d)
+    assert code.n == d * d + (d - 1) ** 2
+    assert len(code.z_checks) == d * (d - 1) and len(code.x_checks) == d * (d - 1)
+    hz, hx = parity_check_matrices(code)
+    assert not ((hx.astype(int) @ hz.T.astype(int)) % 2).any()
+    for h in (hz, hx):
+        deg = h.sum(axis=0)
+        assert deg.min() >= 1 and deg.max() <= 2
+        assert set(h.sum(axis=1)) <= {3, 4} or d == 2
+    zl = np.zeros(code.n, dtype=int)
+    zl[code.zl] = 1
+    xl = np.zeros(code.n, dtype=int)
+    xl[code.xl] = 1
+    assert not ((hx @ zl) % 2).any() and not ((hz @ xl) % 2).any() and (zl @ xl) % 2 == 1
+    for kind in ("X", "Z"):
+        g = code_capacity_graph(code, kind)
+        assert _odd_cycle_through_boundary(g) == d
