@@ -94,6 +94,8 @@ typedef struct {
     uint64_t defects;          /* sum over shots and types of s */
     uint64_t forced_runs;      /* forced-convergence runs */
     uint64_t forced_rounds;    /* rounds of locally dominant choices summed over those runs */
+    uint64_t unconverged_any;  /* shots with at least one type never converged (r_nc) */
+    uint64_t conv_fail_any;    /* shots with every type converged and a failure */
 } bp4m_counts;
 
 typedef struct {

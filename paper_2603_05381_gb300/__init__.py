@@ -153,4 +153,5 @@ class Graph:
         return {"shots": c.shots, "fail": list(c.fail), "unconverged": list(c.unconverged),
                 "forced_output": list(c.forced_output), "conv_fail": list(c.conv_fail),
                 "iterations": c.iterations, "msg_updates": c.msg_updates, "defects": c.defects,
-                "forced_runs": c.forced_runs, "forced_rounds": c.forced_rounds}
+                "forced_runs": c.forced_runs, "forced_rounds": c.forced_rounds,
+                "unconverged_any": c.unconverged_any, "conv_fail_any": c.conv_fail_any}

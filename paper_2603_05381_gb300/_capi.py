@@ -42,7 +42,8 @@ class Counts(ctypes.Structure):
                 ("unconverged", ctypes.c_uint64 * 2), ("forced_output", ctypes.c_uint64 * 2),
                 ("conv_fail", ctypes.c_uint64 * 2), ("iterations", ctypes.c_uint64),
                 ("msg_updates", ctypes.c_uint64), ("defects", ctypes.c_uint64),
-                ("forced_runs", ctypes.c_uint64), ("forced_rounds", ctypes.c_uint64)]
+                ("forced_runs", ctypes.c_uint64), ("forced_rounds", ctypes.c_uint64),
+                ("unconverged_any", ctypes.c_uint64), ("conv_fail_any", ctypes.c_uint64)]
 
 
 class GraphInfo(ctypes.Structure):

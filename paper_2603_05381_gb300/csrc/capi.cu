@@ -338,10 +338,9 @@ int decode_device(bp4m_graph* g, int ty, const uint32_t* synd, int64_t shots, in
     const int n_glob = w.host_small[kGlobalTier];
     if (n_glob > 0) {
         const int max_s = w.host_small[2 * kTiers];
-        const int gsmax = (max_s + 63) / 64 * 64;
-        const size_t esz = prec == 0 ? sizeof(double) : sizeof(float);
-        const size_t slot_bytes = (size_t)3 * gsmax * gsmax * esz;
-        int slots = std::min(n_glob, 2 * g->num_sms);
+        int gsmax = 0;
+        const size_t slot_bytes = global_slot_bytes(prec, max_s, &gsmax);
+        int slots = std::min(n_glob, g->num_sms);
         const size_t budget = (size_t)16 << 30;
         while (slots > 1 && (size_t)slots * slot_bytes > budget) --slots;
         int rc = ensure_gscratch(g, (size_t)slots * slot_bytes);
@@ -350,7 +349,7 @@ int decode_device(bp4m_graph* g, int ty, const uint32_t* synd, int64_t shots, in
         a.count = w.small + kGlobalTier;
         a.next = w.small + kTiers + kGlobalTier;
         a.gscratch = w.gscratch;
-        a.gslot_elems = (int64_t)gsmax * gsmax;
+        a.gslot_elems = (int64_t)(slot_bytes / (prec == 0 ? sizeof(double) : sizeof(float)) / 3);
         a.gsmax = gsmax;
         a.tier = kGlobalTier;
         ProfScope ps(g, PROF_GLOBAL, st);
@@ -377,6 +376,8 @@ void fill_counts(const unsigned long long* c, int n_types, bp4m_counts* out) {
     out->defects = c[C_DEFECTS];
     out->forced_runs = c[C_FC_RUNS];
     out->forced_rounds = c[C_FC_ROUNDS];
+    out->unconverged_any = c[C_UNCONV_ANY];
+    out->conv_fail_any = c[C_CONVFAIL_ANY];
 }
 
 int sample_into(bp4m_graph* g, uint64_t first_shot, int64_t shots, uint64_t seed, uint32_t sid,

@@ -29,6 +29,8 @@ enum CounterSlot {
     C_TIER_SHOTS = C_TIER_MSGS + 7,  // 7 slots: shots per decode tier
     C_FC_RUNS = C_TIER_SHOTS + 7,    // forced-convergence runs
     C_FC_ROUNDS,                     // locally-dominant rounds summed over runs
+    C_UNCONV_ANY,                    // shots with at least one unconverged type
+    C_CONVFAIL_ANY,                  // shots with every type converged and some type failed
     C_NUM
 };
 
@@ -110,7 +112,9 @@ cudaError_t launch_classify(const uint32_t* synd, int64_t shots, int n_words,
 // (0 = FP64, 1 = FP32).  Returns cudaSuccess if the tier is empty by construction.
 cudaError_t launch_decode_tier(int precision, int tier, const DecodeArgs& a, int num_sms,
                                cudaStream_t st);
-// Global-memory tier.  `slots` CTAs each own one scratch slot.
+// Global-memory tier.  `slots` CTAs each own one scratch slot of global_slot_bytes() for
+// the batch's largest defect count; a.gsmax must be the value that function reports.
+size_t global_slot_bytes(int precision, int max_s, int* gsmax_out);
 cudaError_t launch_decode_global(int precision, const DecodeArgs& a, int slots,
                                  cudaStream_t st);
 // Shared-memory tier plan for a precision.

@@ -147,7 +147,9 @@ __device__ __forceinline__ void combine_max(T& m1, T& m2, int& k, T o1, T o2, in
 // memory) runs two blocks per SM; the others are limited by shared memory or 128 registers.
 __host__ __device__ constexpr int blocks_for(int nt) { return nt == 384 ? 2 : min_blocks(nt); }
 
-template <typename T, int CH, int G, bool TRACE>
+// REG = true keeps each thread's own outputs M[i][k] in registers between iterations (no
+// strided shared-memory read per message); REG = false reads them back from Mt[k][i].
+template <typename T, int CH, int G, bool TRACE, bool REG>
 __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G)) decode_smem_kernel(const DecodeArgs a) {
     constexpr int SMAX = CH * G;
     constexpr int NT = SMAX * G;
@@ -248,6 +250,9 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G)) decode_sme
 
         const bool act = i < s;
         T q[CH];
+        T mo[REG ? CH : 1];
+        int am_prev = -1;          // REG: argmax column of the previous update and its output
+        T out_am = T(0);
         int t = 0;
         bool any_conv = false, forced_ran = false;
         int out_par = 0, out_forced = 0, out_from_best = 0;
@@ -270,7 +275,7 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G)) decode_sme
                     for (int c = 0; c < CH; ++c) {
                         const T l = row_l[G * c];
                         const T x = row_m[G * c];
-                        const T own = col_m[G * P * c];
+                        const T own = REG ? mo[REG ? c : 0] : col_m[G * P * c];
                         q[c] = B2<T>::fma_(x, ainv, l);
                         const T lam = l + (own + x);
                         if (c & 1)
@@ -281,11 +286,18 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G)) decode_sme
                             trl[((size_t)shot * a.s_cap + i) * a.s_cap + g + G * c] = lam * (T)kLn2;
                     }
                     bits = b0 | b1;
-                    if (own_diag) {
+                    if (!REG && own_diag) {
                         // the boundary variable v_ii: lambda_ii = l_ii + M[i][i]
                         const T lam = Lm[i * P + i] + Dg[i];
                         bits = (bits & ~((Mask)1 << c_diag)) | ((Mask)(lam > T(0) ? 1u : 0u) << c_diag);
                         if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + i] = lam * (T)kLn2;
+                    }
+                    if (REG && am_prev % G == g) {
+                        // the argmax column's own output is out_am, not the generic formula's
+                        const int ca = am_prev / G;
+                        const T lam = Lm[i * P + am_prev] + (out_am + Mt[i * P + am_prev]);
+                        bits = (bits & ~((Mask)1 << ca)) | ((Mask)(lam > T(0) ? 1u : 0u) << ca);
+                        if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + am_prev] = lam * (T)kLn2;
                     }
                 }
             }
@@ -310,7 +322,7 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G)) decode_sme
                     forced_ran = true;
                     if (act && g == 0) matched[i] = 0;
                     __syncthreads();
-                    const T lii = act ? Lm[i * P + i] + Dg[i] : ninf;
+                    const T lii = act ? (REG ? Lm[i * P + i] + (mo[REG ? c_diag : 0] + T(0)) : Lm[i * P + i] + Dg[i]) : ninf;
                     for (int round = 0; round < s; ++round) {
                         const bool open = act && !matched[i];
                         T bl = ninf;
@@ -320,8 +332,10 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G)) decode_sme
                             for (int c = 0; c < CH; ++c) {
                                 const int k = g + G * c;
                                 if (k == i || !matched[k]) {
-                                    T lam = row_l[G * c] + (col_m[G * P * c] + row_m[G * c]);
-                                    if (k == i) lam = lii;
+                                    const T own = REG ? mo[REG ? c : 0] : col_m[G * P * c];
+                                    T lam = row_l[G * c] + (own + row_m[G * c]);
+                                    if (!REG && k == i) lam = lii;
+                                    if (REG && k == am_prev) lam = row_l[G * c] + (out_am + row_m[G * c]);
                                     if (bk < 0 || lam > bl) {
                                         bl = lam;
                                         bk = k;
@@ -468,10 +482,19 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G)) decode_sme
                 const T Aa = B2<T>::fma_(cf, S - T(1), T(1));
                 if (act) {
 #pragma unroll
-                    for (int c = 0; c < CH; ++c) col_m[G * P * c] = -m1 - B2<T>::lg2(B2<T>::fma_(-cf, q[c], Aa));
-                    if (am % G == g) Mt[am * P + i] = -m2 - B2<T>::lg2(S - T(1));
+                    for (int c = 0; c < CH; ++c) {
+                        const T out = -m1 - B2<T>::lg2(B2<T>::fma_(-cf, q[c], Aa));
+                        col_m[G * P * c] = out;
+                        if (REG) mo[REG ? c : 0] = out;
+                    }
+                    const T oam = -m2 - B2<T>::lg2(S - T(1));
+                    if (am % G == g) Mt[am * P + i] = oam;
+                    if (REG) {
+                        am_prev = am;
+                        out_am = oam;
+                    }
                     if (own_diag) {
-                        Dg[i] = Mt[i * P + i];
+                        if (!REG) Dg[i] = Mt[i * P + i];
                         Mt[i * P + i] = T(0);
                     }
                 }
@@ -801,6 +824,345 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
     }
 }
 
+// ------------------------------------------------------------------ streaming tier
+//
+// Shots with more unsatisfied detectors than the shared-memory tiers hold.  One warp owns
+// one factor row at a time (its CH*32 columns in registers); the shot's matrices live in a
+// per-block scratch slot in global memory (L2-resident for the sizes this tier meets):
+//   Lg[r][k]     prior l_rk in log2 units, -inf for k >= s          (ld = 32*CH columns)
+//   Mt[b][r][k]  incoming message M[k][r], double buffered (b = iteration parity)
+//   Mo[r][k]     the row's own outputs M[r][k], updated in place by the owning warp
+// The diagonal of Mt is kept 0, so Q_rr = l_rr and lambda_rr = l_rr + Mo[r][r].  Outputs go
+// to Mt[next][k][r]; a batch of kStreamWarps consecutive rows stages them in shared memory
+// and writes kStreamWarps consecutive floats per column k.  Iteration = decision pass
+// (lambda of the previous update, convergence vote, candidates / forced convergence), then
+// the update pass.
+constexpr int kStreamWarps = 16;
+constexpr int kStreamThreads = kStreamWarps * 32;
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v = B2<T>::mx(v, __shfl_xor_sync(kFull, v, off));
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+    return v;
+}
+
+template <typename T, int CH, bool TRACE>
+__global__ void __launch_bounds__(kStreamThreads, 1) decode_stream_kernel(const DecodeArgs a) {
+    constexpr int LD = 32 * CH;
+    constexpr int SP = LD + 1;  // stage pitch: odd, so the transposed read is conflict-free
+    extern __shared__ __align__(16) unsigned char smem[];
+    T* stage = reinterpret_cast<T*>(smem);                          // [kStreamWarps][SP]
+    double* rowacc = reinterpret_cast<double*>(stage + kStreamWarps * SP + ((kStreamWarps * SP) & 1));
+    int* dets = reinterpret_cast<int*>(rowacc + LD);
+    int* choice = dets + LD;
+    short* bestp = reinterpret_cast<short*>(choice + LD);
+    unsigned char* matched = reinterpret_cast<unsigned char*>(bestp + LD);
+    __shared__ int sh_item, sh_s, sh_best_par, sh_best_forced, sh_improve, sh_use_best;
+    __shared__ double sh_best_w;
+
+    const size_t mat = (size_t)LD * LD;
+    T* slot = reinterpret_cast<T*>(a.gscratch) + (size_t)blockIdx.x * 4 * mat;
+    T* Lg = slot;
+    T* Mtb[2] = {slot + mat, slot + 2 * mat};
+    T* Mo = slot + 3 * mat;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = a.tb.n_det;
+    const T* __restrict__ Ltab = Num<T>::L(a.tb);
+    const int64_t count = a.count ? (int64_t)*a.count : a.count_val;
+    const T ainv = (T)(1.0 / a.alpha);
+    const bool full = (a.decoder == 1) || !a.early_exit;
+    T* trl = reinterpret_cast<T*>(a.tr_lambda);
+    const T ninf = Num<T>::ninf();
+    unsigned long long acc_it = 0, acc_msg = 0, acc_def = 0, acc_shots = 0, acc_fc = 0, acc_fcr = 0;
+
+    for (;;) {
+        if (tid == 0) sh_item = atomicAdd(a.next, 1);
+        __syncthreads();
+        const int item = sh_item;
+        if (item >= count) break;
+        const int64_t shot = a.list ? (int64_t)a.list[item] : (int64_t)item;
+        if (warp == 0) {
+            const int s0 = compact_defects(a.synd + (size_t)shot * a.tb.n_words, a.tb.n_words, dets, LD, lane);
+            if (lane == 0) sh_s = s0;
+        }
+        __syncthreads();
+        const int s = sh_s;
+        if (s > LD || s < 2) {
+            if (tid == 0 && a.ctr) atomicAdd(a.ctr + C_ERRORS, 1ull);
+            continue;
+        }
+        const bool tr_on = TRACE && s <= a.s_cap;
+        for (int r = warp; r < s; r += kStreamWarps) {
+            const T* trow = Ltab + (size_t)dets[r] * n;
+            for (int k = lane; k < LD; k += 32) {
+                Lg[(size_t)r * LD + k] = k < s ? (T)(__ldg(trow + dets[k]) * (T)kLog2e) : ninf;
+                Mtb[0][(size_t)r * LD + k] = T(0);
+                Mtb[1][(size_t)r * LD + k] = T(0);
+                Mo[(size_t)r * LD + k] = T(0);
+            }
+        }
+        for (int r = tid; r < LD; r += kStreamThreads) {
+            matched[r] = r >= s;
+            bestp[r] = -1;
+        }
+        if (tid == 0) {
+            sh_best_w = Num<double>::pinf();
+            sh_best_par = 0;
+            sh_best_forced = 0;
+            sh_use_best = 0;
+        }
+        __syncthreads();
+
+        int cur = 0;
+        int t = 0;
+        bool any_conv = false, forced_ran = false;
+        int out_par = 0, out_forced = 0, out_from_best = 0;
+
+        for (;;) {
+            const T* Mc = Mtb[cur];
+            if (t > 0) {
+                // ---- decisions of lambda^t = l + (M[r][k] + M[k][r])
+                int ok_all = 1;
+                for (int r = warp; r < s; r += kStreamWarps) {
+                    const T* lrow = Lg + (size_t)r * LD;
+                    const T* xrow = Mc + (size_t)r * LD;
+                    const T* orow = Mo + (size_t)r * LD;
+                    int cnt = 0, chosen = 0x7fffffff;
+#pragma unroll
+                    for (int c = 0; c < CH; ++c) {
+                        const int k = lane + 32 * c;
+                        const T lam = lrow[k] + (orow[k] + xrow[k]);
+                        const bool keep = lam > T(0);
+                        const unsigned bal = __ballot_sync(kFull, keep);
+                        cnt += __popc(bal);
+                        if (bal && chosen == 0x7fffffff) chosen = 32 * c + __ffs(bal) - 1;
+                        if (tr_on && trl && k < s) trl[((size_t)shot * a.s_cap + r) * a.s_cap + k] = lam * (T)kLn2;
+                    }
+                    if (lane == 0) choice[r] = chosen;
+                    ok_all &= (cnt == 1);
+                }
+                const int conv = __syncthreads_and(ok_all);
+                bool have_cand = false, cand_forced = false;
+                if (conv) {
+                    any_conv = true;
+                    have_cand = true;
+                } else if (a.decoder == 1 || t == a.T) {
+                    // ---- forced convergence on lambda^t by locally dominant rounds
+                    forced_ran = true;
+                    for (int r = tid; r < s; r += kStreamThreads) matched[r] = 0;
+                    __syncthreads();
+                    for (int round = 0; round < s; ++round) {
+                        for (int r = warp; r < s; r += kStreamWarps) {
+                            if (matched[r]) continue;  // uniform per warp
+                            const T* lrow = Lg + (size_t)r * LD;
+                            const T* xrow = Mc + (size_t)r * LD;
+                            const T* orow = Mo + (size_t)r * LD;
+                            T bl = ninf;
+                            int bk = 0x7fffffff;
+#pragma unroll
+                            for (int c = 0; c < CH; ++c) {
+                                const int k = lane + 32 * c;
+                                if (k < s && (k == r || !matched[k])) {
+                                    const T lam = lrow[k] + (orow[k] + xrow[k]);
+                                    if (bk == 0x7fffffff || lam > bl) {
+                                        bl = lam;
+                                        bk = k;
+                                    }
+                                }
+                            }
+#pragma unroll
+                            for (int off = 16; off; off >>= 1) {
+                                const T ol = __shfl_xor_sync(kFull, bl, off);
+                                const int okk = __shfl_xor_sync(kFull, bk, off);
+                                if (okk != 0x7fffffff && (bk == 0x7fffffff || ol > bl || (ol == bl && okk < bk))) {
+                                    bl = ol;
+                                    bk = okk;
+                                }
+                            }
+                            if (lane == 0) choice[r] = bk != 0x7fffffff ? bk : r;
+                        }
+                        __syncthreads();
+                        int left = 0;
+                        for (int r = tid; r < s; r += kStreamThreads) {
+                            if (matched[r]) continue;
+                            const int pk = choice[r];
+                            const bool newm = (pk == r) || (choice[pk] == r);
+                            rowacc[r] = newm ? 1.0 : 0.0;
+                            left += !newm;
+                        }
+                        __syncthreads();
+                        for (int r = tid; r < s; r += kStreamThreads)
+                            if (!matched[r] && rowacc[r] != 0.0) matched[r] = 1;
+                        if (tid == 0) acc_fcr += 1;
+                        if (__syncthreads_count(left) == 0) break;
+                    }
+                    if (tid == 0) acc_fc += 1;
+                    have_cand = true;
+                    cand_forced = true;
+                }
+                if (have_cand) {
+                    int pc = 0;
+                    for (int r = tid; r < s; r += kStreamThreads) {
+                        const int k = choice[r];
+                        double w = 0.0;
+                        if (k >= r) {
+                            const size_t off = (size_t)dets[r] * n + dets[k];
+                            pc ^= a.tb.P[off];
+                            if (full) w = a.tb.W64[off];
+                        }
+                        rowacc[r] = w;
+                    }
+                    const int par = __syncthreads_count(pc) & 1;
+                    bool finish = false;
+                    if (!full) {
+                        out_par = par;
+                        out_forced = cand_forced;
+                        finish = true;
+                    } else {
+                        if (tid == 0) {
+                            double w = 0.0;
+                            for (int r = 0; r < s; ++r) w += rowacc[r];
+                            sh_improve = 0;
+                            sh_use_best = 0;
+                            if (a.decoder == 1 || !cand_forced) {
+                                if (w < sh_best_w) {
+                                    sh_best_w = w;
+                                    sh_best_par = par;
+                                    sh_best_forced = cand_forced;
+                                    sh_improve = 1;
+                                }
+                            } else {
+                                sh_use_best = sh_best_w <= w;
+                            }
+                        }
+                        __syncthreads();
+                        if (sh_improve)
+                            for (int r = tid; r < s; r += kStreamThreads) bestp[r] = (short)choice[r];
+                        if (t == a.T || (a.decoder == 0 && cand_forced)) {
+                            finish = true;
+                            if (a.decoder == 0 && cand_forced && !sh_use_best) {
+                                out_par = par;
+                                out_forced = 1;
+                            } else {
+                                out_par = sh_best_par;
+                                out_forced = sh_best_forced;
+                                out_from_best = 1;
+                            }
+                        }
+                        __syncthreads();
+                    }
+                    if (finish) break;
+                }
+                __syncthreads();
+            }
+            // ---- update pass: M' for every row, batch by batch
+            T* Mn = Mtb[cur ^ 1];
+            const int nbatch = (s + kStreamWarps - 1) / kStreamWarps;
+            for (int b = 0; b < nbatch; ++b) {
+                const int r = b * kStreamWarps + warp;
+                T* srow = stage + warp * SP;
+                if (r < s) {
+                    const T* lrow = Lg + (size_t)r * LD;
+                    const T* xrow = Mc + (size_t)r * LD;
+                    T* orow = Mo + (size_t)r * LD;
+                    T q[CH];
+                    T m1 = ninf, m2 = ninf;
+                    int am = 0x7fffffff;
+#pragma unroll
+                    for (int c = 0; c < CH; ++c) {
+                        const int k = lane + 32 * c;
+                        const T v = B2<T>::fma_(xrow[k], ainv, lrow[k]);
+                        q[c] = v;
+                        const bool gt = v > m1;
+                        m2 = B2<T>::mx(m2, B2<T>::mn(v, m1));
+                        m1 = B2<T>::mx(m1, v);
+                        am = gt ? k : am;
+                    }
+#pragma unroll
+                    for (int off = 16; off; off >>= 1) {
+                        const T o1 = __shfl_xor_sync(kFull, m1, off);
+                        const T o2 = __shfl_xor_sync(kFull, m2, off);
+                        const int ok = __shfl_xor_sync(kFull, am, off);
+                        combine_max(m1, m2, am, o1, o2, ok);
+                    }
+                    T S = T(0);
+#pragma unroll
+                    for (int c = 0; c < CH; ++c) {
+                        const T u = B2<T>::ex2(B2<T>::mn(q[c], m2) - m2);
+                        q[c] = u;
+                        S += u;
+                    }
+                    S = warp_sum(S);
+                    const T cf = B2<T>::ex2(m2 - m1);
+                    const T Aa = B2<T>::fma_(cf, S - T(1), T(1));
+#pragma unroll
+                    for (int c = 0; c < CH; ++c) {
+                        const int k = lane + 32 * c;
+                        const T out = -m1 - B2<T>::lg2(B2<T>::fma_(-cf, q[c], Aa));
+                        orow[k] = out;
+                        srow[k] = out;
+                    }
+                    if ((am & 31) == lane) {
+                        const T oam = -m2 - B2<T>::lg2(S - T(1));
+                        orow[am] = oam;
+                        srow[am] = oam;
+                    }
+                    __syncwarp();
+                    if (lane == 0) srow[r] = T(0);  // the diagonal of Mt stays 0
+                }
+                __syncthreads();
+                // transposed write of the batch: Mn[k][b*W + w] = stage[w][k]
+                const int r0 = b * kStreamWarps;
+                const int rows = min(kStreamWarps, s - r0);
+                for (int e = tid; e < s * kStreamWarps; e += kStreamThreads) {
+                    const int k = e / kStreamWarps, w = e % kStreamWarps;
+                    if (w < rows) Mn[(size_t)k * LD + r0 + w] = stage[w * SP + k];
+                }
+                __syncthreads();
+            }
+            cur ^= 1;
+            ++t;
+        }
+        if (tr_on && a.tr_partner) {
+            for (int r = tid; r < a.s_cap; r += kStreamThreads) {
+                int pk = -1;
+                if (r < s) pk = out_from_best ? (int)bestp[r] : choice[r];
+                a.tr_partner[(size_t)shot * a.s_cap + r] = (int16_t)pk;
+            }
+        }
+        if (tid == 0) {
+            if (a.obs_pred) a.obs_pred[shot] = (uint8_t)out_par;
+            if (a.flags)
+                a.flags[shot] = (uint8_t)((any_conv ? F_CONVERGED : 0) | (forced_ran ? F_FORCED_RAN : 0) |
+                                          (out_forced ? F_FROM_FORCED : 0));
+            if (a.iters) a.iters[shot] = (int16_t)t;
+            acc_it += (unsigned long long)t;
+            acc_msg += (unsigned long long)s * s * t;
+            acc_def += (unsigned long long)s;
+            acc_shots += 1;
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && a.ctr) {
+        atomicAdd(a.ctr + C_ITERS, acc_it);
+        atomicAdd(a.ctr + C_MSGS, acc_msg);
+        atomicAdd(a.ctr + C_DEFECTS, acc_def);
+        atomicAdd(a.ctr + C_TIER_MSGS + a.tier, acc_msg);
+        atomicAdd(a.ctr + C_TIER_SHOTS + a.tier, acc_shots);
+        atomicAdd(a.ctr + C_FC_RUNS, acc_fc);
+        atomicAdd(a.ctr + C_FC_ROUNDS, acc_fcr);
+    }
+}
+
 // ------------------------------------------------------------------ no-allocation scratch
 //
 // bp4m_decode_noalloc serves callers that cannot allocate device memory.  Its scratch is
@@ -828,6 +1190,9 @@ struct TierCfg {
 // FP32: 32/64/96/128/160 rows in shared memory; FP64: 32/64/112 (tiers 4, 5 unused).
 constexpr TierCfg kCfg32[6] = {{0, 0, 0}, {32, 32, 1}, {64, 32, 2}, {96, 24, 4}, {128, 32, 4}, {160, 40, 4}};
 constexpr TierCfg kCfg64[6] = {{0, 0, 0}, {32, 16, 2}, {64, 16, 4}, {112, 28, 4}, {112, 28, 4}, {112, 28, 4}};
+// FP32 tiers that keep their own outputs in registers (the 96- and 160-row tiers have no
+// register room for them).
+constexpr bool kReg32[6] = {false, true, true, false, true, false};
 
 template <typename T, int CH, int G>
 size_t smem_bytes_of() {
@@ -837,10 +1202,10 @@ size_t smem_bytes_of() {
            (size_t)SMAX * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 16;
 }
 
-template <typename T, int CH, int G, bool TRACE>
+template <typename T, int CH, int G, bool TRACE, bool REG>
 cudaError_t run_tier(const DecodeArgs& a, int num_sms, cudaStream_t st, bool prepare_only) {
     const size_t smem = smem_bytes_of<T, CH, G>();
-    auto kern = decode_smem_kernel<T, CH, G, TRACE>;
+    auto kern = decode_smem_kernel<T, CH, G, TRACE, REG>;
     if (prepare_only)
         return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per_sm = 0;
@@ -851,12 +1216,16 @@ cudaError_t run_tier(const DecodeArgs& a, int num_sms, cudaStream_t st, bool pre
     return cudaGetLastError();
 }
 
-template <typename T, int CH, int G>
-cudaError_t run_tier2(const DecodeArgs& a, int num_sms, cudaStream_t st, bool prep, bool trace) {
-    cudaError_t e = run_tier<T, CH, G, false>(a, num_sms, st, prep);
-    if (prep && e == cudaSuccess) return run_tier<T, CH, G, true>(a, num_sms, st, prep);
-    if (prep || !trace) return e;
-    return run_tier<T, CH, G, true>(a, num_sms, st, prep);
+// Every tier has a production instantiation and a traced one (tests).
+template <typename T, int CH, int G, bool REG>
+cudaError_t run_tier2(const DecodeArgs& a, int num_sms, cudaStream_t st, bool prep) {
+    const bool tr = a.tr_lambda != nullptr || a.tr_partner != nullptr;
+    if (prep) {
+        cudaError_t e = run_tier<T, CH, G, false, REG>(a, num_sms, st, true);
+        return e != cudaSuccess ? e : run_tier<T, CH, G, true, REG>(a, num_sms, st, true);
+    }
+    return tr ? run_tier<T, CH, G, true, REG>(a, num_sms, st, false)
+              : run_tier<T, CH, G, false, REG>(a, num_sms, st, false);
 }
 
 template <typename T>
@@ -864,44 +1233,23 @@ cudaError_t dispatch_tier(int tier, const DecodeArgs& a, int num_sms, cudaStream
 
 template <>
 cudaError_t dispatch_tier<float>(int tier, const DecodeArgs& a, int num_sms, cudaStream_t st, bool prep) {
-    const bool tr = a.tr_lambda != nullptr || a.tr_partner != nullptr;
-    if (!prep && tr) {
-        switch (tier) {
-            case 1: return run_tier<float, 32, 1, true>(a, num_sms, st, false);
-            case 2: return run_tier<float, 32, 2, true>(a, num_sms, st, false);
-            case 3: return run_tier<float, 24, 4, true>(a, num_sms, st, false);
-            case 4: return run_tier<float, 32, 4, true>(a, num_sms, st, false);
-            case 5: return run_tier<float, 40, 4, true>(a, num_sms, st, false);
-            default: return cudaErrorInvalidValue;
-        }
-    }
     switch (tier) {
-        case 1: return run_tier2<float, 32, 1>(a, num_sms, st, prep, false);
-        case 2: return run_tier2<float, 32, 2>(a, num_sms, st, prep, false);
-        case 3: return run_tier2<float, 24, 4>(a, num_sms, st, prep, false);
-        case 4: return run_tier2<float, 32, 4>(a, num_sms, st, prep, false);
-        case 5: return run_tier2<float, 40, 4>(a, num_sms, st, prep, false);
+        case 1: return run_tier2<float, 32, 1, kReg32[1]>(a, num_sms, st, prep);
+        case 2: return run_tier2<float, 32, 2, kReg32[2]>(a, num_sms, st, prep);
+        case 3: return run_tier2<float, 24, 4, kReg32[3]>(a, num_sms, st, prep);
+        case 4: return run_tier2<float, 32, 4, kReg32[4]>(a, num_sms, st, prep);
+        case 5: return run_tier2<float, 40, 4, kReg32[5]>(a, num_sms, st, prep);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <>
 cudaError_t dispatch_tier<double>(int tier, const DecodeArgs& a, int num_sms, cudaStream_t st, bool prep) {
-    const bool tr = a.tr_lambda != nullptr || a.tr_partner != nullptr;
-    if (!prep && tr) {
-        switch (tier) {
-            case 1: return run_tier<double, 16, 2, true>(a, num_sms, st, false);
-            case 2: return run_tier<double, 16, 4, true>(a, num_sms, st, false);
-            case 3: return run_tier<double, 28, 4, true>(a, num_sms, st, false);
-            case 4: case 5: return cudaSuccess;  // same bound as tier 3: never populated
-            default: return cudaErrorInvalidValue;
-        }
-    }
     switch (tier) {
-        case 1: return run_tier2<double, 16, 2>(a, num_sms, st, prep, false);
-        case 2: return run_tier2<double, 16, 4>(a, num_sms, st, prep, false);
-        case 3: return run_tier2<double, 28, 4>(a, num_sms, st, prep, false);
-        case 4: case 5: return cudaSuccess;
+        case 1: return run_tier2<double, 16, 2, false>(a, num_sms, st, prep);
+        case 2: return run_tier2<double, 16, 4, false>(a, num_sms, st, prep);
+        case 3: return run_tier2<double, 28, 4, false>(a, num_sms, st, prep);
+        case 4: case 5: return cudaSuccess;  // same bound as tier 3: never populated
         default: return cudaErrorInvalidValue;
     }
 }
@@ -980,8 +1328,57 @@ cudaError_t launch_decode_noalloc(int precision, DecodeArgs a, int64_t shots, cu
     return cudaSuccess;
 }
 
+namespace {
+
+template <typename T, int CH>
+cudaError_t run_stream(const DecodeArgs& a, int slots, cudaStream_t st) {
+    constexpr int LD = 32 * CH;
+    const size_t smem = (size_t)kStreamWarps * (LD + 1) * sizeof(T) + sizeof(T) +
+                        (size_t)LD * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 16;
+    const bool tr = a.tr_lambda != nullptr || a.tr_partner != nullptr;
+    auto kern = tr ? decode_stream_kernel<T, CH, true> : decode_stream_kernel<T, CH, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<slots, kStreamThreads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Columns per lane of the streaming kernel for the largest defect count of a batch; 0 when
+// the general global kernel takes the batch.
+int stream_ch(int precision, int max_s) {
+    if (max_s <= 256) return 8;
+    if (max_s <= 512) return 16;
+    if (precision != 0 && max_s <= 1024) return 32;
+    return 0;
+}
+
+}  // namespace
+
+size_t global_slot_bytes(int precision, int max_s, int* gsmax_out) {
+    const size_t esz = precision == 0 ? sizeof(double) : sizeof(float);
+    const int ch = stream_ch(precision, max_s);
+    if (ch) {
+        const size_t ld = 32 * (size_t)ch;
+        *gsmax_out = (int)ld;
+        return 4 * ld * ld * esz;
+    }
+    const int gsmax = (max_s + 63) / 64 * 64;
+    *gsmax_out = gsmax;
+    return (size_t)3 * gsmax * gsmax * esz;
+}
+
 cudaError_t launch_decode_global(int precision, const DecodeArgs& a, int slots, cudaStream_t st) {
     if (slots <= 0) return cudaSuccess;
+    const int ch = stream_ch(precision, a.gsmax);
+    if (ch && 32 * ch == a.gsmax) {
+        if (precision == 0) {
+            if (ch == 8) return run_stream<double, 8>(a, slots, st);
+            return run_stream<double, 16>(a, slots, st);
+        }
+        if (ch == 8) return run_stream<float, 8>(a, slots, st);
+        if (ch == 16) return run_stream<float, 16>(a, slots, st);
+        return run_stream<float, 32>(a, slots, st);
+    }
     const size_t smem = (size_t)a.gsmax * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 16;
     cudaError_t e;
     if (precision == 0) {

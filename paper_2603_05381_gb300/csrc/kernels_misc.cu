@@ -169,20 +169,24 @@ __global__ void __launch_bounds__(kCntThreads) count_kernel(
     for (int64_t shot = (int64_t)blockIdx.x * kCntThreads + threadIdx.x; shot < shots;
          shot += (int64_t)gridDim.x * kCntThreads) {
         c[C_SHOTS] += 1;
-        bool any = false;
+        bool any = false, all_conv = true;
         for (int ty = 0; ty < n_types; ++ty) {
             const size_t k = (size_t)ty * shots + shot;
             const bool fail = obs_true[k] != obs_pred[k];
             const uint8_t f = flags[k];
             any |= fail;
+            all_conv &= (f & F_CONVERGED) != 0;
             c[C_FAIL_X + ty] += fail;
             c[C_UNCONV_X + ty] += !(f & F_CONVERGED);
             c[C_FORCED_X + ty] += (f & F_FROM_FORCED) ? 1 : 0;
             c[C_CONVFAIL_X + ty] += (fail && (f & F_CONVERGED)) ? 1 : 0;
         }
         c[C_FAIL_ANY] += any;
+        c[C_UNCONV_ANY] += !all_conv;
+        c[C_CONVFAIL_ANY] += (all_conv && any) ? 1 : 0;
     }
-    for (int k = 0; k < C_ITERS; ++k) {
+    for (int k = 0; k < C_NUM; ++k) {
+        if (k >= C_ITERS && k != C_UNCONV_ANY && k != C_CONVFAIL_ANY) continue;
         unsigned long long v = c[k];
 #pragma unroll
         for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);

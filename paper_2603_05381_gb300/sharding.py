@@ -7,7 +7,7 @@ per-rank counters (u64 counts), done once per run.
 """
 
 COUNT_KEYS = ("shots", "fail", "unconverged", "forced_output", "conv_fail", "iterations",
-              "msg_updates", "defects", "forced_runs", "forced_rounds")
+              "msg_updates", "defects", "forced_runs", "forced_rounds", "unconverged_any", "conv_fail_any")
 
 
 def shot_range(rank, world, step, shots_per_rank, first=0):

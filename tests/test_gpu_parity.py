@@ -202,12 +202,13 @@ def _random_syndromes(n_det, sizes, seed):
 def test_every_tier_boundary_d13(torch, prec, early):
     # defect counts on both sides of every shared-memory tier bound and in the global tier
     g, og, ot = circuit_pair(13, 0.005)
-    sizes = [0, 1, 2, 3, 31, 32, 33, 63, 64, 65, 111, 112, 113, 127, 128, 129, 159, 160, 161, 200]
+    sizes = [0, 1, 2, 3, 31, 32, 33, 63, 64, 65, 95, 96, 97, 111, 112, 113, 127, 128, 129, 159, 160,
+             161, 200, 256, 257, 300]
     sb = _random_syndromes(og.n_det, sizes, seed=17 + early)
     synd = torch.as_tensor(pack_syndromes(sb).view(np.int32), device="cuda")
     T = 6
     opts = pkg.make_opts(precision=prec, early_exit=early)
-    res = gpu_decode(g, synd, T, opts, s_cap=208)
+    res = gpu_decode(g, synd, T, opts, s_cap=304)
     assert list(res["s"]) == sizes
     tau = TAU64 if prec == "fp64" else TAU32
     cnt, bad = compare_shots(ot, sb, res, T, range(len(sizes)), tau, early_exit=early)
@@ -261,3 +262,29 @@ def test_bench_workload_d13_sampled_shots(torch):
     assert counts["shots"] == n and counts["fail"][0] == fails
     assert counts["unconverged"][0] == int((conv.cpu().numpy() == 0).sum())
     assert counts["iterations"] == int(its.cpu().numpy().astype(np.int64).sum())
+
+
+# ------------------------------------------------------------------ unrotated code
+
+
+def test_unrotated_sampler_and_decoding(torch):
+    from oracle.surface import unrotated_code
+    d, p = 5, 0.006
+    g = pkg.Graph(d, "circuit", p, family="unrotated")
+    og, _, _ = circuit_graph(d, Noise(p), "unrotated")
+    ot = circuit_tables(og)
+    n, T = 300, 25
+    (synd,), obs = gpu_sample(g, 99, n, seed=4)
+    osyn, oobs = graph_sample(og, np.arange(99, 99 + n), seed=4)
+    assert np.array_equal(as_bool(synd, og.n_det), osyn) and np.array_equal(obs[0].cpu().numpy(), oobs)
+    for prec, tau in (("fp64", TAU64), ("fp32", TAU32)):
+        res = gpu_decode(g, synd, T, pkg.make_opts(precision=prec, early_exit=False), s_cap=96)
+        cnt, bad = compare_shots(ot, osyn, res, T, range(n), tau, early_exit=False)
+        assert all(m < tau for _, m in bad), bad
+    gc = pkg.Graph(7, "code_capacity", 0.1, family="unrotated")
+    synds, obsc = gpu_sample(gc, 0, 2000, seed=2)
+    ref = code_capacity_sample(unrotated_code(7), 0.1, np.arange(2000), seed=2)
+    for ty, kind in ((0, "X"), (1, "Z")):
+        n_det = gc.info()["n_det"][ty]
+        assert np.array_equal(as_bool(synds[ty], n_det), ref[kind][0])
+        assert np.array_equal(obsc[ty].cpu().numpy(), ref[kind][1])

@@ -22,8 +22,9 @@ def _counts_for_range(start, stop):
     samp = code_capacity_sample(code, P, np.arange(start, stop), seed=SEED)
     c = {"shots": stop - start, "fail": [0, 0, 0], "unconverged": [0, 0], "forced_output": [0, 0],
          "conv_fail": [0, 0], "iterations": 0, "msg_updates": 0, "defects": 0, "forced_runs": 0,
-         "forced_rounds": 0}
+         "forced_rounds": 0, "unconverged_any": 0, "conv_fail_any": 0}
     anyf = np.zeros(stop - start, dtype=bool)
+    allconv = np.ones(stop - start, dtype=bool)
     for ty, kind in ((0, "X"), (1, "Z")):
         tb = code_capacity_tables(code_capacity_graph(code, kind), P)
         synd, obs = samp[kind]
@@ -33,10 +34,13 @@ def _counts_for_range(start, stop):
             anyf[k] |= f
             c["fail"][ty] += int(f)
             c["unconverged"][ty] += int(not r.converged)
+            allconv[k] &= bool(r.converged)
             c["iterations"] += r.iters
             c["msg_updates"] += r.msg_updates
             c["defects"] += int(synd[k].sum())
     c["fail"][2] = int(anyf.sum())
+    c["unconverged_any"] = int((~allconv).sum())
+    c["conv_fail_any"] = int((allconv & anyf).sum())
     return c
 
 
