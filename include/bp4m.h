@@ -69,14 +69,17 @@ typedef struct {
 #define BP4M_FP64 0
 #define BP4M_FP32 1
 
-#define BP4M_DEC_BP4M  0   /* Sec. "Belief Propagation for Matching (BP4M)" */
-#define BP4M_DEC_BP4MF 1   /* Sec. "BP4M Forced (BP4MF)"; alpha != 1 gives Memory-BP4MF */
+#define BP4M_DEC_BP4M   0  /* Sec. "Belief Propagation for Matching (BP4M)" */
+#define BP4M_DEC_BP4MF  1  /* Sec. "BP4M Forced (BP4MF)"; alpha != 1 gives Memory-BP4MF */
+#define BP4M_DEC_BBP4MF 2  /* Sec. "Belief-BP4MF (B-BP4MF)", code capacity only: quaternary BP on
+                              the Tanner graph, then BP4MF on priors reweighted by its posteriors */
 
 typedef struct {
     int precision;   /* BP4M_FP64 or BP4M_FP32: message storage and arithmetic */
     int early_exit;  /* BP4M only. 1: output the first converged iteration.
                         0: run all iterations, keep the lightest converged candidate */
-    int decoder;     /* BP4M_DEC_BP4M or BP4M_DEC_BP4MF */
+    int decoder;     /* BP4M_DEC_BP4M, BP4M_DEC_BP4MF or (sample_and_decode, code capacity)
+                        BP4M_DEC_BBP4MF */
     double alpha;    /* variable-update memory parameter (Sec. "BP Improvements"); 1 = plain */
     int type;        /* code capacity only: 0 = X errors on the Z-check graph,
                         1 = Z errors on the X-check graph.  Ignored for circuits. */
@@ -178,6 +181,20 @@ int bp4m_sample_and_decode(bp4m_graph* g, double p, int64_t shots, uint64_t seed
 int bp4m_sample_and_decode_range(bp4m_graph* g, uint64_t first_shot, int64_t shots,
                                  uint64_t seed, uint32_t stream_id, int iters,
                                  const bp4m_opts* opts, bp4m_counts* out, void* stream);
+
+/* B-BP4MF (Sec. "Belief-BP4MF (B-BP4MF)" and Sec. "Correlated decoding") on code-capacity
+   graphs.  First stage: quaternary BP on the Tanner graph with `iters` iterations and the
+   graph's p as the depolarizing prior; a shot whose hard decision reproduces its syndrome
+   takes that decision.  Otherwise, per type, every data qubit's edge of the decoding graph is
+   weighted max(ln((1-P)/P), 2^-20) with P its posterior of an error component of that type
+   (the floor keeps shortest paths defined when P >= 1/2, a case the paper does not treat),
+   Dijkstra from every unsatisfied check yields the shot's priors, and BP4MF (alpha from
+   opts) runs for `iters` iterations.  At most 160 (FP32) or 112 (FP64) unsatisfied checks
+   of a type per shot (BP4M_EUNSUPPORTED beyond).  syndromes: uint32 [2][shots][n_words] (type 0 then type 1, the layout of
+   bp4m_sample); outputs obs_pred and flags (bit0 converged, bit3 first stage): uint8
+   [2][shots]; flags may be NULL.  Host or device buffers.  Synchronises `stream`. */
+int bp4m_decode_bbp4mf(bp4m_graph* g, const uint32_t* syndromes, int64_t shots, int iters,
+                       const bp4m_opts* opts, uint8_t* obs_pred, uint8_t* flags, void* stream);
 
 /* Decoding without any device allocation.  The paper has no counterpart: this entry point
    exists for callers that cannot call cudaMalloc, such as a decoding service that must

@@ -9,7 +9,8 @@ every data qubit is an edge of G_D between its one or two checks (one check: to 
 boundary), with weight ln((1 - P_e)/P_e) where P_e is the posterior probability that the
 qubit carries an error component detected by that check type; Dijkstra from every
 unsatisfied check gives the shot's pair and boundary weights, hence its priors
-(Eq. two-syn var factors with the reweighted w), and BP4MF runs on them.
+(Eq. two-syn var factors with the reweighted w), and BP4MF runs on them.  Edge weights are
+floored at MIN_WEIGHT (posteriors >= 1/2; see below).
 
 Quaternary BP (the paper cites it without restating it; this is the standard form with
 one scalar message per Tanner edge):
@@ -37,6 +38,11 @@ PAULIS = ("I", "X", "Y", "Z")
 # anticommutation of E with an X-type / Z-type check
 ANTI_X = np.array([0, 0, 1, 1])  # I, X, Y, Z vs X-check: Y, Z anticommute
 ANTI_Z = np.array([0, 1, 1, 0])  # vs Z-check: X, Y anticommute
+# Smallest reweighted edge weight.  A posterior at or above one half gives ln((1-P)/P) <= 0,
+# and on an undirected graph a non-positive edge leaves no minimum-weight path (a negative
+# edge can be walked back and forth); the paper does not treat this case, so such weights
+# are raised to 2^-20 (the path then costs almost nothing and its prior is large but finite).
+MIN_WEIGHT = 2.0 ** -20
 
 
 def tanner(code):
@@ -99,7 +105,7 @@ def reweighted_tables(g, edge_prob, dets, through_boundary=False):
     weights = []
     for e, (u, v, ob, _) in enumerate(g.edges):
         pe = min(max(float(edge_prob[e]), 1e-300), 1.0 - 1e-16)
-        weights.append(math.log((1.0 - pe) / pe))
+        weights.append(max(math.log((1.0 - pe) / pe), MIN_WEIGHT))
     adj = adjacency(g, weights)
     s = len(dets)
     W = np.full((s, s), np.inf)

@@ -12,8 +12,8 @@ import ctypes
 import numpy as np
 
 from . import _capi
-from ._capi import (CIRCUIT, CODE_CAPACITY, DEC_BP4M, DEC_BP4MF, FP32, FP64, PRIOR_2P3, PRIOR_P,
-                    Bp4mError, check, load)
+from ._capi import (CIRCUIT, CODE_CAPACITY, DEC_BBP4MF, DEC_BP4M, DEC_BP4MF, FP32, FP64, PRIOR_2P3,
+                    PRIOR_P, Bp4mError, check, load)
 
 __all__ = ["Graph", "Bp4mError", "load", "version", "FP32", "FP64", "DEC_BP4M", "DEC_BP4MF"]
 
@@ -52,7 +52,8 @@ def _stream(stream):
 
 
 def make_opts(precision=FP32, early_exit=True, decoder="bp4m", alpha=1.0, type=0):
-    dec = {"bp4m": DEC_BP4M, "bp4mf": DEC_BP4MF}[decoder] if isinstance(decoder, str) else int(decoder)
+    dec = ({"bp4m": DEC_BP4M, "bp4mf": DEC_BP4MF, "bbp4mf": DEC_BBP4MF}[decoder] if isinstance(decoder, str)
+           else int(decoder))
     prec = {"fp32": FP32, "fp64": FP64}[precision] if isinstance(precision, str) else int(precision)
     return _capi.Opts(prec, 1 if early_exit else 0, dec, float(alpha), int(type))
 
@@ -133,6 +134,12 @@ class Graph:
         tr = _capi.Trace(_ptr(lam), _ptr(partner), _ptr(defects), _ptr(flags), int(s_cap))
         check(load().bp4m_decode_trace(self._h, _ptr(syndromes), int(syndromes.shape[0]), int(iters),
                                        ctypes.byref(opts), _ptr(obs_pred), ctypes.byref(tr), _stream(stream)))
+
+    def decode_bbp4mf(self, syndromes, iters, opts, obs_pred, flags=None, stream=None):
+        """B-BP4MF on both types: syndromes uint32 [2][shots][words] (flat), outputs uint8 [2][shots]."""
+        shots = obs_pred.shape[-1]
+        check(load().bp4m_decode_bbp4mf(self._h, _ptr(syndromes), int(shots), int(iters), ctypes.byref(opts),
+                                        _ptr(obs_pred), _ptr(flags), _stream(stream)))
 
     def profile_enable(self, on=True):
         """Start (and reset) or stop event timing of every kernel launch of this graph."""

@@ -19,6 +19,7 @@ FP64 = 0
 FP32 = 1
 DEC_BP4M = 0
 DEC_BP4MF = 1
+DEC_BBP4MF = 2
 EXPORT_W, EXPORT_L, EXPORT_PARITY, EXPORT_EDGES, EXPORT_THRESH = range(5)
 
 
@@ -87,6 +88,7 @@ SIGNATURES = {
     "bp4m_sample_and_decode_range": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint64,
                                                     ctypes.c_uint32, ctypes.c_int, ctypes.POINTER(Opts),
                                                     ctypes.POINTER(Counts), _P]),
+    "bp4m_decode_bbp4mf": (ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(Opts), _P, _P, _P]),
     "bp4m_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "bp4m_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "bp4m_free_graph": (None, [_P]),

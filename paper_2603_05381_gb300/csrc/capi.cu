@@ -8,6 +8,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "bp4m.h"
@@ -77,6 +78,12 @@ struct Workspace {
     void* gscratch = nullptr;
     size_t gscratch_bytes = 0;
     cudaEvent_t ev_small = nullptr;
+    // B-BP4MF first stage
+    int64_t qcap = 0;
+    uint8_t* qconv = nullptr;
+    uint8_t* qobs = nullptr;     // [2][qcap]
+    int16_t* qiters = nullptr;
+    double* post = nullptr;      // [2][qcap][n_units]
 };
 
 struct bp4m_graph {
@@ -91,6 +98,13 @@ struct bp4m_graph {
     uint32_t* thr = nullptr;
     uint32_t* uvo = nullptr;
     uint32_t* cc_uvo = nullptr;
+    // code capacity, B-BP4MF: Tanner graph and per-type CSR adjacency
+    int* chk_q = nullptr;
+    int* q_edge = nullptr;
+    uint8_t* in_zl = nullptr;
+    uint8_t* in_xl = nullptr;
+    int* rw_off[2] = {nullptr, nullptr};
+    uint32_t* rw_adj[2] = {nullptr, nullptr};
     int64_t table_bytes = 0;
     bool prepared[2] = {false, false};
     Workspace ws;
@@ -212,6 +226,66 @@ int ensure_uploaded(bp4m_graph* g) {
         CK(dalloc(&g->cc_uvo, cc.size()));
         CK(cudaMemcpy(g->cc_uvo, cc.data(), cc.size() * 4, cudaMemcpyHostToDevice));
         g->table_bytes += (int64_t)cc.size() * 4;
+        // Tanner graph for quaternary BP: X-checks (type 1 detectors) first, then Z-checks
+        const int n = h.n_units, nx = h.t[1].n_det, nz = h.t[0].n_det, nc = nx + nz;
+        std::vector<std::vector<int>> cq(nc);
+        for (int q = 0; q < n; ++q) {
+            for (int ty = 1; ty >= 0; --ty) {
+                const int off = ty == 1 ? 0 : nx;
+                cq[off + h.cc_u[ty][q]].push_back(q);
+                if (h.cc_v[ty][q] < h.t[ty].n_det) cq[off + h.cc_v[ty][q]].push_back(q);
+            }
+        }
+        std::vector<int> chk_q(4 * (size_t)nc, -1), q_edge(4 * (size_t)n, -1), qdeg(n, 0);
+        for (int c = 0; c < nc; ++c) {
+            std::sort(cq[c].begin(), cq[c].end());
+            if (cq[c].size() > 4) return fail(BP4M_EUNSUPPORTED, "a check of weight > 4");
+            for (size_t j = 0; j < cq[c].size(); ++j) {
+                const int q = cq[c][j];
+                chk_q[4 * c + j] = q;
+                if (qdeg[q] >= 4) return fail(BP4M_EUNSUPPORTED, "a qubit in more than 4 checks");
+                q_edge[4 * q + qdeg[q]++] = 4 * c + (int)j;
+            }
+        }
+        std::vector<uint8_t> zl(n), xl(n);
+        for (int q = 0; q < n; ++q) {
+            zl[q] = h.cc_obs[0][q];
+            xl[q] = h.cc_obs[1][q];
+        }
+        CK(dalloc(&g->chk_q, chk_q.size()));
+        CK(dalloc(&g->q_edge, q_edge.size()));
+        CK(dalloc(&g->in_zl, n));
+        CK(dalloc(&g->in_xl, n));
+        CK(cudaMemcpy(g->chk_q, chk_q.data(), chk_q.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(g->q_edge, q_edge.data(), q_edge.size() * 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(g->in_zl, zl.data(), n, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(g->in_xl, xl.data(), n, cudaMemcpyHostToDevice));
+        // decoding-graph adjacency per type: entries (neighbour, qubit, obs) sorted per node by
+        // (neighbour, obs, qubit), so that among equal-weight parallel edges the obs-0 one is
+        // relaxed first
+        for (int ty = 0; ty < 2; ++ty) {
+            const int nd = h.t[ty].n_det;
+            std::vector<std::vector<std::tuple<int, int, int>>> adj(nd + 1);
+            for (int q = 0; q < n; ++q) {
+                const int u = h.cc_u[ty][q], v = h.cc_v[ty][q], ob = h.cc_obs[ty][q];
+                adj[u].emplace_back(v, ob, q);
+                adj[v].emplace_back(u, ob, q);
+            }
+            std::vector<int> off(nd + 2, 0);
+            std::vector<uint32_t> ent;
+            for (int u = 0; u <= nd; ++u) {
+                std::sort(adj[u].begin(), adj[u].end());
+                off[u] = (int)ent.size();
+                for (auto& e : adj[u])
+                    ent.push_back((uint32_t)std::get<0>(e) | ((uint32_t)std::get<2>(e) << 15) |
+                                  ((uint32_t)std::get<1>(e) << 31));
+            }
+            off[nd + 1] = (int)ent.size();
+            CK(dalloc(&g->rw_off[ty], off.size()));
+            CK(dalloc(&g->rw_adj[ty], ent.size()));
+            CK(cudaMemcpy(g->rw_off[ty], off.data(), off.size() * 4, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(g->rw_adj[ty], ent.data(), ent.size() * 4, cudaMemcpyHostToDevice));
+        }
     }
     g->uploaded = true;
     return BP4M_OK;
@@ -230,6 +304,10 @@ void free_ws(Workspace& w) {
     cudaFreeHost(w.host_small);
     cudaFreeHost(w.host_ctr);
     if (w.ev_small) cudaEventDestroy(w.ev_small);
+    cudaFree(w.qconv);
+    cudaFree(w.qobs);
+    cudaFree(w.qiters);
+    cudaFree(w.post);
     w = Workspace();
 }
 
@@ -272,12 +350,34 @@ int ensure_gscratch(bp4m_graph* g, size_t bytes) {
     return BP4M_OK;
 }
 
+int ensure_qbp_ws(bp4m_graph* g, int64_t cap) {
+    Workspace& w = g->ws;
+    if (w.qcap >= cap) return BP4M_OK;
+    cudaFree(w.qconv);
+    cudaFree(w.qobs);
+    cudaFree(w.qiters);
+    cudaFree(w.post);
+    w.qconv = nullptr;
+    w.qobs = nullptr;
+    w.qiters = nullptr;
+    w.post = nullptr;
+    w.qcap = 0;
+    CK(dalloc(&w.qconv, cap));
+    CK(dalloc(&w.qobs, 2 * (size_t)cap));
+    CK(dalloc(&w.qiters, cap));
+    CK(dalloc(&w.post, 2 * (size_t)cap * g->host.n_units));
+    w.qcap = cap;
+    return BP4M_OK;
+}
+
 int check_opts(const bp4m_graph* g, const bp4m_opts* o, int iters) {
     if (!o) return fail(BP4M_EINVAL, "opts is NULL");
     if (o->precision != BP4M_FP64 && o->precision != BP4M_FP32)
         return fail(BP4M_EINVAL, "precision must be BP4M_FP64 or BP4M_FP32");
-    if (o->decoder != BP4M_DEC_BP4M && o->decoder != BP4M_DEC_BP4MF)
+    if (o->decoder != BP4M_DEC_BP4M && o->decoder != BP4M_DEC_BP4MF && o->decoder != BP4M_DEC_BBP4MF)
         return fail(BP4M_EINVAL, "unknown decoder");
+    if (o->decoder == BP4M_DEC_BBP4MF && g->host.model != BP4M_CODE_CAPACITY)
+        return fail(BP4M_EUNSUPPORTED, "B-BP4MF is implemented for code-capacity noise");
     if (!(o->alpha > 0.0)) return fail(BP4M_EINVAL, "alpha must be positive");
     if (iters < 1 || iters > 30000) return fail(BP4M_EINVAL, "iters must be in [1, 30000]");
     if (g->host.n_types == 2 && (o->type < 0 || o->type > 1))
@@ -287,9 +387,17 @@ int check_opts(const bp4m_graph* g, const bp4m_opts* o, int iters) {
 
 // Decodes `shots` device-resident syndromes of type `ty`; results go to the given device
 // arrays (obs_pred / flags / iters are required here).
+// B-BP4MF second stage inputs of decode_device.
+struct Stage2 {
+    const uint8_t* skip = nullptr;      // shots resolved by the first stage
+    const uint8_t* skip_obs = nullptr;
+    const int16_t* skip_iters = nullptr;
+    const double* post = nullptr;       // [shots][n_units] posteriors of this type
+};
+
 int decode_device(bp4m_graph* g, int ty, const uint32_t* synd, int64_t shots, int T,
                   const bp4m_opts* o, uint8_t* obs_pred, uint8_t* flags, int16_t* iters,
-                  const bp4m_trace* tr, cudaStream_t st) {
+                  const bp4m_trace* tr, cudaStream_t st, const Stage2* rw = nullptr) {
     Workspace& w = g->ws;
     const int prec = o->precision == BP4M_FP64 ? 0 : 1;
     if (!g->prepared[prec]) {
@@ -301,7 +409,8 @@ int decode_device(bp4m_graph* g, int ty, const uint32_t* synd, int64_t shots, in
     {
         ProfScope ps(g, PROF_CLASSIFY, st);
         CK(launch_classify(synd, shots, n_words_of(g, ty), plan, w.lists, w.small, w.small + 2 * kTiers,
-                           obs_pred, flags, iters, tr ? tr->defects : nullptr, st));
+                           obs_pred, flags, iters, tr ? tr->defects : nullptr, rw ? rw->skip : nullptr,
+                           rw ? rw->skip_obs : nullptr, rw ? rw->skip_iters : nullptr, st));
         ps.end();
     }
     CK(cudaMemcpyAsync(w.host_small, w.small, (2 * kTiers + 1) * sizeof(int32_t),
@@ -324,6 +433,44 @@ int decode_device(bp4m_graph* g, int ty, const uint32_t* synd, int64_t shots, in
         a.tr_partner = tr->partner;
         a.tr_defects = tr->defects;
         a.s_cap = tr->s_cap;
+    }
+    if (rw) {
+        // second stage of B-BP4MF: BP4MF on the reweighted priors, shared-memory tiers only
+        a.decoder = BP4M_DEC_BP4MF;
+        a.rw_post = rw->post;
+        a.rw_off = g->rw_off[ty];
+        a.rw_adj = g->rw_adj[ty];
+        a.rw_units = g->host.n_units;
+        const int max_tier = prec == 0 ? kRwMaxTier64 : kRwMaxTier32;
+        // the tiers run one after another on `st` and share the scratch; each launch has
+        // its own grid and slot size
+        size_t need = 0;
+        int64_t slot[kTiers] = {};
+        for (int tier = 1; tier <= max_tier; ++tier) {
+            const size_t b = rw_scratch_bytes(prec, tier, g->host.t[ty].n_det, g->num_sms, &slot[tier]);
+            if (b == 0) return fail(BP4M_ECUDA, "B-BP4MF: no launch configuration for a reweighting tier");
+            need = std::max(need, b);
+        }
+        int rc = ensure_gscratch(g, need);
+        if (rc) return rc;
+        a.gscratch = w.gscratch;
+        a.gscratch_bytes = (int64_t)w.gscratch_bytes;
+        for (int tier = 1; tier <= max_tier; ++tier) {
+            a.rw_slot_bytes = slot[tier];
+            a.list = w.lists + (size_t)tier * shots;
+            a.count = w.small + tier;
+            a.next = w.small + kTiers + tier;
+            a.tier = tier;
+            ProfScope ps(g, tier, st);
+            CK(launch_decode_tier_rw(prec, tier, a, g->num_sms, st));
+            ps.end();
+        }
+        CK(cudaEventSynchronize(w.ev_small));
+        for (int tier = max_tier + 1; tier < kTiers; ++tier)
+            if (w.host_small[tier] > 0)
+                return fail(BP4M_EUNSUPPORTED, prec == 0 ? "B-BP4MF (FP64) decodes at most 112 unsatisfied checks of a type per shot"
+                                                         : "B-BP4MF (FP32) decodes at most 160 unsatisfied checks of a type per shot");
+        return BP4M_OK;
     }
     for (int tier = 1; tier < kGlobalTier; ++tier) {
         a.list = w.lists + (size_t)tier * shots;
@@ -358,6 +505,56 @@ int decode_device(bp4m_graph* g, int ty, const uint32_t* synd, int64_t shots, in
     }
     return BP4M_OK;
 }
+
+// B-BP4MF on device-resident syndromes of both types (type 1 = X-checks, type 0 = Z-checks).
+int bbp4mf_device(bp4m_graph* g, const uint32_t* synd0, const uint32_t* synd1, int64_t shots, int T,
+                  const bp4m_opts* o, uint8_t* obs_pred, uint8_t* flags, int16_t* iters, cudaStream_t st) {
+    int rc = ensure_qbp_ws(g, shots);
+    if (rc) return rc;
+    Workspace& w = g->ws;
+    const int prec = o->precision == BP4M_FP64 ? 0 : 1;
+    QbpArgs q;
+    q.shots = shots;
+    q.T = T;
+    q.p = g->host.p;
+    q.clamp = prec == 0 ? 1e-15 : 2.384185791015625e-07;
+    q.n_qubits = g->host.n_units;
+    q.n_xchecks = g->host.t[1].n_det;
+    q.n_checks = g->host.t[1].n_det + g->host.t[0].n_det;
+    q.n_words[0] = n_words_of(g, 0);
+    q.n_words[1] = n_words_of(g, 1);
+    q.synd0 = synd0;
+    q.synd1 = synd1;
+    q.chk_q = g->chk_q;
+    q.q_edge = g->q_edge;
+    q.in_zl = g->in_zl;
+    q.in_xl = g->in_xl;
+    q.qconv = w.qconv;
+    q.qobs = w.qobs;
+    q.qiters = w.qiters;
+    q.post = w.post;
+    {
+        ProfScope ps(g, PROF_CLASSIFY, st);
+        CK(launch_qbp(prec, q, g->num_sms, st));
+        ps.end();
+    }
+    bp4m_opts o2 = *o;
+    o2.decoder = BP4M_DEC_BP4MF;
+    for (int ty = 0; ty < 2; ++ty) {
+        Stage2 s2;
+        s2.skip = w.qconv;
+        s2.skip_obs = w.qobs + (size_t)ty * shots;
+        s2.skip_iters = w.qiters;
+        s2.post = w.post + (size_t)ty * shots * g->host.n_units;
+        o2.type = ty;
+        rc = decode_device(g, ty, ty == 0 ? synd0 : synd1, shots, T, &o2, obs_pred + (size_t)ty * shots,
+                           flags + (size_t)ty * shots, iters + (size_t)ty * shots, nullptr, st, &s2);
+        if (rc) return rc;
+    }
+    return BP4M_OK;
+}
+
+constexpr int64_t kBbpBatch = (int64_t)1 << 17;
 
 void fill_counts(const unsigned long long* c, int n_types, bp4m_counts* out) {
     std::memset(out, 0, sizeof(*out));
@@ -559,6 +756,8 @@ static int decode_common(bp4m_graph* g, const uint32_t* syndromes, int64_t shots
     int rc = check_opts(g, opts, iters);
     if (rc) return rc;
     if (tr && (tr->s_cap < 1 || tr->s_cap > 4096)) return fail(BP4M_EINVAL, "trace s_cap out of range");
+    if (opts->decoder == BP4M_DEC_BBP4MF)
+        return fail(BP4M_EINVAL, "B-BP4MF decodes both Pauli types together: use bp4m_decode_bbp4mf");
     if (shots == 0) return BP4M_OK;
     rc = ensure_uploaded(g);
     if (rc) return rc;
@@ -636,7 +835,8 @@ int bp4m_sample_and_decode_range(bp4m_graph* g, uint64_t first_shot, int64_t sho
     rc = ensure_uploaded(g);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t cap = std::min(kBatch, shots);
+    const bool bbp = opts->decoder == BP4M_DEC_BBP4MF;
+    const int64_t cap = std::min(bbp ? kBbpBatch : kBatch, shots);
     rc = ensure_ws(g, std::max<int64_t>(cap, g->ws.cap));
     if (rc) return rc;
     Workspace& w = g->ws;
@@ -646,6 +846,15 @@ int bp4m_sample_and_decode_range(bp4m_graph* g, uint64_t first_shot, int64_t sho
         const int64_t nb = std::min(cap, shots - off);
         rc = sample_into(g, first_shot + (uint64_t)off, nb, seed, stream_id, w.synd, w.obs_true, st);
         if (rc) return rc;
+        if (bbp) {
+            rc = bbp4mf_device(g, w.synd, w.synd + (size_t)nb * n_words_of(g, 0), nb, iters, opts, w.obs_pred,
+                               w.flags, w.iters, st);
+            if (rc) return rc;
+            ProfScope ps(g, PROF_COUNT, st);
+            CK(launch_count(w.obs_true, w.obs_pred, w.flags, nb, nt, w.ctr, st));
+            ps.end();
+            continue;
+        }
         size_t woff = 0;
         for (int ty = 0; ty < nt; ++ty) {
             bp4m_opts o = *opts;
@@ -672,6 +881,43 @@ int bp4m_sample_and_decode(bp4m_graph* g, double p, int64_t shots, uint64_t seed
     if (!g) return fail(BP4M_EINVAL, "null graph");
     if (p != g->host.p) return fail(BP4M_EINVAL, "p differs from the graph's p; build a graph for it");
     return bp4m_sample_and_decode_range(g, 0, shots, seed, 0, iters, opts, out, stream);
+}
+
+int bp4m_decode_bbp4mf(bp4m_graph* g, const uint32_t* syndromes, int64_t shots, int iters,
+                       const bp4m_opts* opts, uint8_t* obs_pred, uint8_t* flags, void* stream) {
+    if (!g || !syndromes || !obs_pred) return fail(BP4M_EINVAL, "null argument");
+    if (g->host.model != BP4M_CODE_CAPACITY) return fail(BP4M_EUNSUPPORTED, "B-BP4MF is implemented for code-capacity noise");
+    if (shots < 0 || shots > ((int64_t)1 << 31)) return fail(BP4M_EINVAL, "shots out of range");
+    if (!opts) return fail(BP4M_EINVAL, "opts is NULL");
+    bp4m_opts o = *opts;
+    o.decoder = BP4M_DEC_BBP4MF;
+    int rc = check_opts(g, &o, iters);
+    if (rc) return rc;
+    if (shots == 0) return BP4M_OK;
+    rc = ensure_uploaded(g);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int nw0 = n_words_of(g, 0), nw1 = n_words_of(g, 1);
+    for (int64_t off = 0; off < shots; off += kBbpBatch) {
+        const int64_t nb = std::min(kBbpBatch, shots - off);
+        rc = ensure_ws(g, std::max<int64_t>(nb, g->ws.cap));
+        if (rc) return rc;
+        Workspace& w = g->ws;
+        CK(cudaMemcpyAsync(w.synd, syndromes + (size_t)off * nw0, (size_t)nb * nw0 * 4, cudaMemcpyDefault, st));
+        CK(cudaMemcpyAsync(w.synd + (size_t)nb * nw0, syndromes + (size_t)shots * nw0 + (size_t)off * nw1,
+                           (size_t)nb * nw1 * 4, cudaMemcpyDefault, st));
+        CK(cudaMemsetAsync(w.ctr, 0, C_NUM * sizeof(unsigned long long), st));
+        rc = bbp4mf_device(g, w.synd, w.synd + (size_t)nb * nw0, nb, iters, &o, w.obs_pred, w.flags, w.iters, st);
+        if (rc) return rc;
+        for (int ty = 0; ty < 2; ++ty) {
+            CK(cudaMemcpyAsync(obs_pred + (size_t)ty * shots + off, w.obs_pred + (size_t)ty * nb, nb,
+                               cudaMemcpyDefault, st));
+            if (flags)
+                CK(cudaMemcpyAsync(flags + (size_t)ty * shots + off, w.flags + (size_t)ty * nb, nb, cudaMemcpyDefault, st));
+        }
+        CK(cudaStreamSynchronize(st));
+    }
+    return BP4M_OK;
 }
 
 int bp4m_decode_noalloc(const bp4m_graph* g, const uint32_t* syndromes, int64_t shots, int iters,
@@ -752,6 +998,14 @@ void bp4m_free_graph(bp4m_graph* g) {
         cudaFree(g->thr);
         cudaFree(g->uvo);
         cudaFree(g->cc_uvo);
+        cudaFree(g->chk_q);
+        cudaFree(g->q_edge);
+        cudaFree(g->in_zl);
+        cudaFree(g->in_xl);
+        for (int ty = 0; ty < 2; ++ty) {
+            cudaFree(g->rw_off[ty]);
+            cudaFree(g->rw_adj[ty]);
+        }
         free_ws(g->ws);
     }
     delete g;

@@ -35,7 +35,7 @@ enum CounterSlot {
 };
 
 // Per-shot result flags.
-enum : uint8_t { F_CONVERGED = 1, F_FORCED_RAN = 2, F_FROM_FORCED = 4 };
+enum : uint8_t { F_CONVERGED = 1, F_FORCED_RAN = 2, F_FROM_FORCED = 4, F_FROM_QBP = 8 };
 
 // Number of s tiers and the per-tier bookkeeping in the workspace.
 constexpr int kTiers = 7;      // tier 0: s == 0 (done in classify), 1..5 shared memory, 6 global
@@ -72,8 +72,20 @@ struct DecodeArgs {
     int64_t count_val = 0;
     int* err_flag = nullptr;         // set to 1 by a block that meets a shot it cannot hold
     int flags_mode = 0;              // 0: `flags` gets F_* bits; 1: `flags` gets converged 0/1
+    // B-BP4MF second stage: the shot's priors come from Dijkstra over per-qubit weights
+    // max(ln((1-P)/P), kRwMinWeight), P = the first stage's posterior (rw_post
+    // [shots][n_units]); adjacency in CSR over n_det + 1 nodes, entries packed
+    // neighbour | unit << 15 | obs << 31, each node's entries sorted by (neighbour, obs).
+    // Per-shot W, parity and Dijkstra state live in a per-block slot of gscratch of
+    // rw_slot_bytes bytes (rw_scratch_bytes()).
+    const double* rw_post = nullptr;
+    const int* rw_off = nullptr;
+    const uint32_t* rw_adj = nullptr;
+    int rw_units = 0;
+    int64_t rw_slot_bytes = 0;
     // global tier: scratch slots
     void* gscratch = nullptr;
+    int64_t gscratch_bytes = 0;      // size of gscratch (checked by the reweighting launches)
     int64_t gslot_elems = 0;         // elements per slot for each of the three matrices
     int gsmax = 0;                   // largest s a slot holds
 };
@@ -97,21 +109,57 @@ struct SampleArgs {
     uint8_t* obs = nullptr;            // [n_types][shots]
 };
 
+struct QbpArgs {
+    int64_t shots = 0;
+    int T = 0;
+    double p = 0.0;
+    double clamp = 1e-15;            // |prod tanh| is kept at most 1 - clamp
+    int n_qubits = 0, n_checks = 0, n_xchecks = 0;
+    int n_words[2] = {0, 0};
+    const uint32_t* synd0 = nullptr;  // type 0 syndromes (Z-checks)
+    const uint32_t* synd1 = nullptr;  // type 1 syndromes (X-checks)
+    const int* chk_q = nullptr;       // [n_checks][4] qubit or -1; X-checks first
+    const int* q_edge = nullptr;      // [n_qubits][4] Tanner edge c*4+j or -1
+    const uint8_t* in_zl = nullptr;
+    const uint8_t* in_xl = nullptr;
+    uint8_t* qconv = nullptr;         // [shots]
+    uint8_t* qobs = nullptr;          // [2][shots]
+    int16_t* qiters = nullptr;        // [shots]
+    double* post = nullptr;           // [2][shots][n_qubits]: P(X comp), P(Z comp)
+};
+
 // ---- launchers (kernels_*.cu) ----
+cudaError_t launch_qbp(int precision, const QbpArgs& a, int num_sms, cudaStream_t st);
 cudaError_t launch_sample_circuit(const SampleArgs& a, cudaStream_t st);
 cudaError_t launch_sample_code_capacity(const SampleArgs& a, cudaStream_t st);
 
 // classify: per shot s = popcount; s == 0 results are written directly; the others are
 // appended to their tier's list.  counts[kTiers], max_s (int) must be zeroed before.
+// With `skip` (per-shot flag) non-null, flagged shots are not decoded: their outputs are
+// taken from skip_obs (the first stage of B-BP4MF) and skip_iters.
 cudaError_t launch_classify(const uint32_t* synd, int64_t shots, int n_words,
                             const TierPlan& plan, int32_t* lists /*[kTiers][shots]*/,
                             int32_t* counts, int32_t* max_s, uint8_t* obs_pred, uint8_t* flags,
-                            int16_t* iters, int32_t* tr_defects, cudaStream_t st);
+                            int16_t* iters, int32_t* tr_defects, const uint8_t* skip,
+                            const uint8_t* skip_obs, const int16_t* skip_iters, cudaStream_t st);
 
 // Launch the decoding kernel of shared-memory tier `tier` (1..5) for precision
 // (0 = FP64, 1 = FP32).  Returns cudaSuccess if the tier is empty by construction.
 cudaError_t launch_decode_tier(int precision, int tier, const DecodeArgs& a, int num_sms,
                                cudaStream_t st);
+// Reweighting (B-BP4MF second stage) decode of the shared-memory tiers (FP32 1..5, FP64
+// 1..3).  rw_scratch_bytes() is the global scratch the launch of `tier` needs for a graph
+// of n_det detectors (one slot per resident block) and sets *slot_bytes; the caller
+// passes that scratch in a.gscratch and the slot size in a.rw_slot_bytes.
+size_t rw_scratch_bytes(int precision, int tier, int n_det, int num_sms, int64_t* slot_bytes);
+cudaError_t launch_decode_tier_rw(int precision, int tier, const DecodeArgs& a, int num_sms,
+                                  cudaStream_t st);
+// Highest shared-memory tier per precision (FP64 tiers 4 and 5 are never populated).
+constexpr int kRwMaxTier32 = 5;
+constexpr int kRwMaxTier64 = 3;
+// Smallest edge weight of the reweighted graph: posteriors at or above one half would give
+// weights <= 0, for which shortest paths do not exist on an undirected graph.
+constexpr double kRwMinWeight = 9.5367431640625e-07;  // 2^-20
 // Global-memory tier.  `slots` CTAs each own one scratch slot of global_slot_bytes() for
 // the batch's largest defect count; a.gsmax must be the value that function reports.
 size_t global_slot_bytes(int precision, int max_s, int* gsmax_out);

@@ -1,539 +1,17 @@
-// BP4M / BP4MF decoding of one shot per thread block.
-//
-// Per shot with s unsatisfied detectors (Sec. "Bipartite Graph Representation"): factor c_i
-// per detector, variable v_ij per pair and v_ii to the boundary; prior LLR l_ij gathered
-// from the per-graph table.  Log-domain sum-product with the flooding schedule (Sec.
-// "Belief Propagation"):
-//   Q[i][k]  = l_ik + M[k][i] / alpha (k != i),  Q[i][i] = l_ii
-//   M'[i][j] = -max*_{k != j} Q[i][k],           max*(x) = ln sum exp(x)
-//   lambda_ij = l_ij + (M'[i][j] + M'[j][i]),    lambda_ii = l_ii + M'[i][i]
-// The leave-one-out max* of a row uses its largest entry m1 (at k = a), second largest m2
-// and S = sum_{k != a} exp(Q_k - m2) >= 1:
-//   j == a:  max*_{k != a} = m2 + ln S
-//   j != a:  max*_{k != j} = m1 + ln(1 + exp(m2 - m1) (S - exp(Q_j - m2)))
-// which is exact algebra, has no cancellation beyond S - exp(Q_j - m2) >= 0, and costs one
-// exp and one log per message.  Marginalization keeps v iff lambda_v > 0; convergence =
-// every factor keeps exactly one variable (Sec. "Checking convergence").  Forced
-// convergence (Sec. "Forced convergence") is the greedy matching in the order
-// (lambda desc, i asc, j asc); it is computed here by rounds of locally dominant
-// choices (a variable that is the best remaining one at both of its factors is accepted),
-// which yields exactly the same matching as the sequential greedy scan.
-//
-// Layout (shared-memory tiers): Mt[i][k] = M[k][i], the message arriving at factor i from
-// the factor k side; Lm[i][k] = l_ik.  Row i is processed by G threads, thread g taking
-// columns k = g + G*c.  The update is in place: every thread caches its row in registers,
-// the block synchronises, then each thread writes its outputs M'[i][k] into Mt[k][i].
+// Decoding kernels for shots that do not fit the shared-memory tiers (global-memory and
+// streaming tiers, the allocation-free entry point) and the dispatch of every tier.
+// The shared-memory kernel and its tier table are in decode_smem.cuh.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cfloat>
 #include <cmath>
-#include <type_traits>
-#include <atomic>
 
+#include "decode_smem.cuh"
 #include "device.cuh"
 
 namespace bp4m {
 namespace {
-
-template <typename T>
-struct Num;
-
-template <>
-struct Num<float> {
-    static __device__ __forceinline__ float ninf() { return __int_as_float(0xff800000); }
-    static __device__ __forceinline__ float pinf() { return __int_as_float(0x7f800000); }
-    static __device__ __forceinline__ float ex(float x) { return __expf(x); }
-    static __device__ __forceinline__ float lg(float x) { return __logf(x); }
-    static __device__ __forceinline__ float lg1p(float x) { return __logf(1.0f + x); }
-    static __device__ __forceinline__ const float* L(const DevTables& t) { return t.L32; }
-};
-
-template <>
-struct Num<double> {
-    static __device__ __forceinline__ double ninf() { return __longlong_as_double(0xfff0000000000000ull); }
-    static __device__ __forceinline__ double pinf() { return __longlong_as_double(0x7ff0000000000000ull); }
-    static __device__ __forceinline__ double ex(double x) { return exp(x); }
-    static __device__ __forceinline__ double lg(double x) { return log(x); }
-    static __device__ __forceinline__ double lg1p(double x) { return log1p(x); }
-    static __device__ __forceinline__ const double* L(const DevTables& t) { return t.L64; }
-};
-
-constexpr unsigned kFull = 0xffffffffu;
-
-// Warp 0 turns the shot's bit-packed syndrome into the sorted detector list.
-__device__ __forceinline__ int compact_defects(const uint32_t* __restrict__ sw, int nw, int* dets,
-                                               int cap, int lane) {
-    int base = 0;
-    for (int w0 = 0; w0 < nw; w0 += 32) {
-        uint32_t word = (w0 + lane < nw) ? __ldg(sw + w0 + lane) : 0u;
-        const int c = __popc(word);
-        int incl = c;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int y = __shfl_up_sync(kFull, incl, off);
-            if (lane >= off) incl += y;
-        }
-        int pos = base + incl - c;
-        while (word) {
-            const int b = __ffs(word) - 1;
-            word &= word - 1;
-            if (pos < cap) dets[pos] = (w0 + lane) * 32 + b;
-            ++pos;
-        }
-        base += __shfl_sync(kFull, incl, 31);
-    }
-    return base;
-}
-
-// Blocks per SM requested from the compiler: enough to keep registers at or below 128.
-__host__ __device__ constexpr int min_blocks(int nt) { return 65536 / (nt * 128) > 1 ? 65536 / (nt * 128) : 1; }
-
-// Base-2 transcendental helpers of the shared-memory tiers: messages are kept in log2
-// units (every prior is scaled by log2(e) when gathered), so exp and log are single
-// ex2/lg2 operations.
-template <typename T>
-struct B2;
-
-template <>
-struct B2<float> {
-    static __device__ __forceinline__ float ex2(float x) {
-        float y;
-        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-        return y;
-    }
-    static __device__ __forceinline__ float lg2(float x) {
-        float y;
-        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-        return y;
-    }
-    static __device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
-    static __device__ __forceinline__ float mx(float a, float b) { return fmaxf(a, b); }
-    static __device__ __forceinline__ float mn(float a, float b) { return fminf(a, b); }
-};
-
-template <>
-struct B2<double> {
-    static __device__ __forceinline__ double ex2(double x) { return exp2(x); }
-    static __device__ __forceinline__ double lg2(double x) { return log2(x); }
-    static __device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
-    static __device__ __forceinline__ double mx(double a, double b) { return fmax(a, b); }
-    static __device__ __forceinline__ double mn(double a, double b) { return fmin(a, b); }
-};
-
-constexpr double kLog2e = 1.4426950408889634074;
-constexpr double kLn2 = 0.69314718055994530942;
-
-// Row pitch in elements.  FP32: pitch = G (mod 32) makes a warp's row reads (R rows x G
-// column groups) hit 32 distinct banks; column accesses are at most 2-way.  FP64: +1.
-template <typename T>
-__host__ __device__ constexpr int pitch_of(int smax, int g) {
-    return sizeof(T) == 8 ? smax + 1 : smax + ((g - smax % 32) % 32 + 32) % 32;
-}
-
-// (max, second max, column of the max) of two partial row scans; ties go to the smaller
-// column.  Commutative, so every thread of a row group ends with the same triple.
-template <typename T>
-__device__ __forceinline__ void combine_max(T& m1, T& m2, int& k, T o1, T o2, int ok) {
-    if (o1 > m1 || (o1 == m1 && ok < k)) {
-        m2 = B2<T>::mx(m1, o2);
-        m1 = o1;
-        k = ok;
-    } else {
-        m2 = B2<T>::mx(m2, o1);
-    }
-}
-
-// Blocks per SM the kernel is compiled for: the 384-thread tier (96 rows, 79 KB of shared
-// memory) runs two blocks per SM; the others are limited by shared memory or 128 registers.
-__host__ __device__ constexpr int blocks_for(int nt) { return nt == 384 ? 2 : min_blocks(nt); }
-
-// REG = true keeps each thread's own outputs M[i][k] in registers between iterations (no
-// strided shared-memory read per message); REG = false reads them back from Mt[k][i].
-template <typename T, int CH, int G, bool TRACE, bool REG>
-__global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G)) decode_smem_kernel(const DecodeArgs a) {
-    constexpr int SMAX = CH * G;
-    constexpr int NT = SMAX * G;
-    constexpr int R = 32 / G;
-    constexpr int P = pitch_of<T>(SMAX, G);
-    static_assert(NT % 32 == 0 && NT <= 1024, "block size");
-    using Mask = typename std::conditional<(CH > 32), unsigned long long, unsigned int>::type;
-    extern __shared__ __align__(16) unsigned char smem[];
-    T* Mt = reinterpret_cast<T*>(smem);          // Mt[i][k] = M[k][i]; diagonal kept 0
-    T* Lm = Mt + SMAX * P;                          // Lm[i][k] = l_ik in log2 units, -inf past s
-    T* Dg = Lm + SMAX * P;                          // Dg[i] = M[i][i] (factor i to its boundary variable)
-    double* rowacc = reinterpret_cast<double*>(Dg + SMAX + (SMAX & 1));
-    int* dets = reinterpret_cast<int*>(rowacc + SMAX);
-    int* choice = dets + SMAX;
-    short* bestp = reinterpret_cast<short*>(choice + SMAX);
-    unsigned char* matched = reinterpret_cast<unsigned char*>(bestp + SMAX);
-    __shared__ int sh_item, sh_s, sh_best_par, sh_best_forced, sh_improve, sh_use_best;
-    __shared__ double sh_best_w;
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int i = warp * R + (lane % R);   // row (factor) of this thread
-    const int g = lane / R;                // column group: columns k = g + G*c
-    const bool own_diag = (i % G) == g;    // this thread holds column k = i of its row
-    const int c_diag = i / G;
-    const int n = a.tb.n_det;
-    const T* __restrict__ Ltab = Num<T>::L(a.tb);
-    const int count = *a.count;
-    const T ainv = (T)(1.0 / a.alpha);
-    const bool full = (a.decoder == 1) || !a.early_exit;
-    T* trl = reinterpret_cast<T*>(a.tr_lambda);
-    const T ninf = Num<T>::ninf();
-    unsigned long long acc_it = 0, acc_msg = 0, acc_def = 0, acc_shots = 0, acc_fc = 0, acc_fcr = 0;
-
-    T* const row_l = Lm + i * P + g;     // element c at [G*c]
-    T* const row_m = Mt + i * P + g;     // incoming messages M[k][i], element c at [G*c]
-    T* const col_m = Mt + g * P + i;     // own outputs M[i][k] live at Mt[k][i], element c at [G*P*c]
-
-    for (;;) {
-        if (tid == 0) sh_item = atomicAdd(a.next, 1);
-        __syncthreads();
-        const int item = sh_item;
-        if (item >= count) break;
-        const int64_t shot = a.list[item];
-        if (warp == 0) {
-            const int s0 = compact_defects(a.synd + (size_t)shot * a.tb.n_words, a.tb.n_words,
-                                           dets, SMAX, lane);
-            if (lane == 0) sh_s = s0;
-        }
-        __syncthreads();
-        const int s = sh_s;
-        if (s > SMAX || s < 1) {
-            if (tid == 0 && a.ctr) atomicAdd(a.ctr + C_ERRORS, 1ull);
-            continue;
-        }
-        const bool tr_on = TRACE && s <= a.s_cap;
-        if (s == 1) {
-            // a single factor with a single variable: the leave-one-out set is empty, the
-            // message is +inf and v_00 is kept in every iteration
-            if (tid == 0) {
-                const int its = full ? a.T : 1;
-                const int d0 = dets[0];
-                if (a.obs_pred) a.obs_pred[shot] = a.tb.P[(size_t)d0 * n + d0];
-                if (a.flags) a.flags[shot] = F_CONVERGED;
-                if (a.iters) a.iters[shot] = (int16_t)its;
-                if (tr_on && trl) trl[(size_t)shot * a.s_cap * a.s_cap] = Num<T>::pinf();
-                if (tr_on && a.tr_partner) {
-                    a.tr_partner[(size_t)shot * a.s_cap] = 0;
-                    for (int k = 1; k < a.s_cap; ++k) a.tr_partner[(size_t)shot * a.s_cap + k] = -1;
-                }
-                acc_it += (unsigned long long)its;
-                acc_msg += (unsigned long long)its;
-                acc_def += 1;
-                acc_shots += 1;
-            }
-            continue;
-        }
-        // ---- gather the shot's priors (log2 units); columns past s are -inf so that they
-        // never win a max, add nothing to a sum and are never kept
-        for (int r = warp; r < s; r += NT / 32) {
-            const T* trow = Ltab + (size_t)dets[r] * n;
-            for (int k = lane; k < SMAX; k += 32) {
-                Lm[r * P + k] = k < s ? (T)(__ldg(trow + dets[k]) * (T)kLog2e) : ninf;
-                Mt[r * P + k] = T(0);
-            }
-        }
-        if (tid < SMAX) {
-            Dg[tid] = T(0);
-            matched[tid] = tid >= s;
-            bestp[tid] = -1;
-        }
-        if (tid == 0) {
-            sh_best_w = Num<double>::pinf();
-            sh_best_par = 0;
-            sh_best_forced = 0;
-            sh_use_best = 0;
-        }
-        __syncthreads();
-
-        const bool act = i < s;
-        T q[CH];
-        T mo[REG ? CH : 1];
-        int am_prev = -1;          // REG: argmax column of the previous update and its output
-        T out_am = T(0);
-        int t = 0;
-        bool any_conv = false, forced_ran = false;
-        int out_par = 0, out_forced = 0, out_from_best = 0;
-        int partner = -1;
-
-        for (;;) {
-            // ---- read phase: Q = l + M[k][i]/alpha for the next update; for t > 0 the
-            // marginalization of lambda^t = l + (M[i][k] + M[k][i])
-            Mask bits = 0;
-            if (!act) {
-#pragma unroll
-                for (int c = 0; c < CH; ++c) q[c] = ninf;
-            } else {
-                if (t == 0) {
-#pragma unroll
-                    for (int c = 0; c < CH; ++c) q[c] = B2<T>::fma_(row_m[G * c], ainv, row_l[G * c]);
-                } else {
-                    Mask b0 = 0, b1 = 0;
-#pragma unroll
-                    for (int c = 0; c < CH; ++c) {
-                        const T l = row_l[G * c];
-                        const T x = row_m[G * c];
-                        const T own = REG ? mo[REG ? c : 0] : col_m[G * P * c];
-                        q[c] = B2<T>::fma_(x, ainv, l);
-                        const T lam = l + (own + x);
-                        if (c & 1)
-                            b1 |= (Mask)(lam > T(0) ? 1u : 0u) << c;
-                        else
-                            b0 |= (Mask)(lam > T(0) ? 1u : 0u) << c;
-                        if (tr_on && trl && g + G * c < s)
-                            trl[((size_t)shot * a.s_cap + i) * a.s_cap + g + G * c] = lam * (T)kLn2;
-                    }
-                    bits = b0 | b1;
-                    if (!REG && own_diag) {
-                        // the boundary variable v_ii: lambda_ii = l_ii + M[i][i]
-                        const T lam = Lm[i * P + i] + Dg[i];
-                        bits = (bits & ~((Mask)1 << c_diag)) | ((Mask)(lam > T(0) ? 1u : 0u) << c_diag);
-                        if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + i] = lam * (T)kLn2;
-                    }
-                    if (REG && am_prev % G == g) {
-                        // the argmax column's own output is out_am, not the generic formula's
-                        const int ca = am_prev / G;
-                        const T lam = Lm[i * P + am_prev] + (out_am + Mt[i * P + am_prev]);
-                        bits = (bits & ~((Mask)1 << ca)) | ((Mask)(lam > T(0) ? 1u : 0u) << ca);
-                        if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + am_prev] = lam * (T)kLn2;
-                    }
-                }
-            }
-            int cnt = sizeof(Mask) == 8 ? __popcll((unsigned long long)bits) : __popc((unsigned)bits);
-            int chosen = bits ? g + G * ((sizeof(Mask) == 8 ? __ffsll((long long)bits) : __ffs((int)bits)) - 1) : -1;
-#pragma unroll
-            for (int off = R; off < 32; off <<= 1) {
-                cnt += __shfl_xor_sync(kFull, cnt, off);
-                chosen = max(chosen, __shfl_xor_sync(kFull, chosen, off));
-            }
-            const int conv = __syncthreads_and(t > 0 && (!act || cnt == 1));
-
-            if (t > 0) {
-                bool have_cand = false, cand_forced = false;
-                int cand_p = -1;
-                if (conv) {
-                    any_conv = true;
-                    have_cand = true;
-                    cand_p = chosen;
-                } else if (a.decoder == 1 || t == a.T) {
-                    // ---- forced convergence on lambda^t by locally dominant rounds
-                    forced_ran = true;
-                    if (act && g == 0) matched[i] = 0;
-                    __syncthreads();
-                    const T lii = act ? (REG ? Lm[i * P + i] + (mo[REG ? c_diag : 0] + T(0)) : Lm[i * P + i] + Dg[i]) : ninf;
-                    for (int round = 0; round < s; ++round) {
-                        const bool open = act && !matched[i];
-                        T bl = ninf;
-                        int bk = -1;
-                        if (open) {
-#pragma unroll
-                            for (int c = 0; c < CH; ++c) {
-                                const int k = g + G * c;
-                                if (k == i || !matched[k]) {
-                                    const T own = REG ? mo[REG ? c : 0] : col_m[G * P * c];
-                                    T lam = row_l[G * c] + (own + row_m[G * c]);
-                                    if (!REG && k == i) lam = lii;
-                                    if (REG && k == am_prev) lam = row_l[G * c] + (out_am + row_m[G * c]);
-                                    if (bk < 0 || lam > bl) {
-                                        bl = lam;
-                                        bk = k;
-                                    }
-                                }
-                            }
-                        }
-#pragma unroll
-                        for (int off = R; off < 32; off <<= 1) {
-                            const T ol = __shfl_xor_sync(kFull, bl, off);
-                            const int ok = __shfl_xor_sync(kFull, bk, off);
-                            if (ok >= 0 && (bk < 0 || ol > bl || (ol == bl && ok < bk))) {
-                                bl = ol;
-                                bk = ok;
-                            }
-                        }
-                        if (open && g == 0) choice[i] = bk >= 0 ? bk : i;
-                        __syncthreads();
-                        bool newm = false;
-                        if (open && g == 0) {
-                            const int pk = choice[i];
-                            newm = (pk == i) || (choice[pk] == i);
-                        }
-                        __syncthreads();
-                        if (newm) matched[i] = 1;
-                        const int left = __syncthreads_count(open && g == 0 && !newm);
-                        if (tid == 0) acc_fcr += 1;
-                        if (left == 0) break;
-                    }
-                    if (tid == 0) acc_fc += 1;
-                    have_cand = true;
-                    cand_forced = true;
-                    if (act && g == 0) cand_p = choice[i];
-                }
-                if (have_cand) {
-                    // ---- candidate parity (and weight when candidates are compared)
-                    int pc = 0;
-                    if (act && g == 0) {
-                        const int k = cand_p;
-                        double w = 0.0;
-                        if (k >= i) {
-                            const size_t off = (size_t)dets[i] * n + dets[k];
-                            pc = a.tb.P[off];
-                            if (full) w = a.tb.W64[off];
-                        }
-                        rowacc[i] = w;
-                    }
-                    const int par = __syncthreads_count(pc) & 1;
-                    bool finish = false;
-                    if (!full) {
-                        out_par = par;
-                        out_forced = cand_forced;
-                        partner = cand_p;
-                        finish = true;
-                    } else {
-                        if (tid == 0) {
-                            double w = 0.0;
-                            for (int r = 0; r < s; ++r) w += rowacc[r];
-                            sh_improve = 0;
-                            sh_use_best = 0;
-                            if (a.decoder == 1 || !cand_forced) {
-                                if (w < sh_best_w) {
-                                    sh_best_w = w;
-                                    sh_best_par = par;
-                                    sh_best_forced = cand_forced;
-                                    sh_improve = 1;
-                                }
-                            } else {
-                                sh_use_best = sh_best_w <= w;
-                            }
-                        }
-                        __syncthreads();
-                        if (sh_improve && act && g == 0) bestp[i] = (short)cand_p;
-                        if (t == a.T || (a.decoder == 0 && cand_forced)) {
-                            finish = true;
-                            if (a.decoder == 0 && cand_forced && !sh_use_best) {
-                                out_par = par;
-                                out_forced = 1;
-                                partner = cand_p;
-                            } else {
-                                out_par = sh_best_par;
-                                out_forced = sh_best_forced;
-                                out_from_best = 1;
-                            }
-                        }
-                        __syncthreads();
-                    }
-                    if (finish) break;
-                }
-            }
-
-            // ---- compute phase: leave-one-out max* of every row, in place.  With m1 (at
-            // column am) and m2 the two largest Q of the row and S = sum_k 2^(min(Q_k, m2) - m2)
-            // (the max clamped to m2, so S - 1 = sum_{k != am} 2^(Q_k - m2) >= 1):
-            //   k != am: M'[i][k] = -(m1 + lg2(1 + 2^(m2 - m1) (S - 1 - 2^(Q_k - m2))))
-            //   k == am: M'[i][k] = -(m2 + lg2(S - 1))
-            {
-                T a1 = ninf, a2 = ninf, b1 = ninf, b2 = ninf;
-                int ac = 0x7fffffff, bc = 0x7fffffff;
-#pragma unroll
-                for (int c = 0; c < CH; c += 2) {
-                    const T v = q[c];
-                    const bool gt = v > a1;
-                    a2 = B2<T>::mx(a2, B2<T>::mn(v, a1));
-                    a1 = B2<T>::mx(a1, v);
-                    ac = gt ? c : ac;
-                    if (c + 1 < CH) {
-                        const T w = q[c + 1];
-                        const bool gw = w > b1;
-                        b2 = B2<T>::mx(b2, B2<T>::mn(w, b1));
-                        b1 = B2<T>::mx(b1, w);
-                        bc = gw ? c + 1 : bc;
-                    }
-                }
-                // column indices of the two partial maxima (ties to the smaller column)
-                int ka = ac < CH ? g + G * ac : 0x7fffffff;
-                int kb = bc < CH ? g + G * bc : 0x7fffffff;
-                combine_max(a1, a2, ka, b1, b2, kb);
-                T m1 = a1, m2 = a2;
-                int am = ka;
-#pragma unroll
-                for (int off = R; off < 32; off <<= 1) {
-                    const T o1 = __shfl_xor_sync(kFull, m1, off);
-                    const T o2 = __shfl_xor_sync(kFull, m2, off);
-                    const int ok = __shfl_xor_sync(kFull, am, off);
-                    combine_max(m1, m2, am, o1, o2, ok);
-                }
-                T sa = T(0), sb = T(0);
-#pragma unroll
-                for (int c = 0; c < CH; c += 2) {
-                    const T u = B2<T>::ex2(B2<T>::mn(q[c], m2) - m2);
-                    q[c] = u;
-                    sa += u;
-                    if (c + 1 < CH) {
-                        const T w = B2<T>::ex2(B2<T>::mn(q[c + 1], m2) - m2);
-                        q[c + 1] = w;
-                        sb += w;
-                    }
-                }
-                T S = sa + sb;
-#pragma unroll
-                for (int off = R; off < 32; off <<= 1) S += __shfl_xor_sync(kFull, S, off);
-                const T cf = B2<T>::ex2(m2 - m1);
-                const T Aa = B2<T>::fma_(cf, S - T(1), T(1));
-                if (act) {
-#pragma unroll
-                    for (int c = 0; c < CH; ++c) {
-                        const T out = -m1 - B2<T>::lg2(B2<T>::fma_(-cf, q[c], Aa));
-                        col_m[G * P * c] = out;
-                        if (REG) mo[REG ? c : 0] = out;
-                    }
-                    const T oam = -m2 - B2<T>::lg2(S - T(1));
-                    if (am % G == g) Mt[am * P + i] = oam;
-                    if (REG) {
-                        am_prev = am;
-                        out_am = oam;
-                    }
-                    if (own_diag) {
-                        if (!REG) Dg[i] = Mt[i * P + i];
-                        Mt[i * P + i] = T(0);
-                    }
-                }
-            }
-            __syncthreads();
-            ++t;
-        }
-
-        // ---- outputs of the shot
-        if (tr_on && a.tr_partner) {
-            if (act && g == 0) {
-                const int pk = out_from_best ? (int)bestp[i] : partner;
-                a.tr_partner[(size_t)shot * a.s_cap + i] = (int16_t)pk;
-            }
-            for (int k = s + tid; k < a.s_cap; k += NT) a.tr_partner[(size_t)shot * a.s_cap + k] = -1;
-        }
-        if (tid == 0) {
-            if (a.obs_pred) a.obs_pred[shot] = (uint8_t)out_par;
-            if (a.flags)
-                a.flags[shot] = (uint8_t)((any_conv ? F_CONVERGED : 0) | (forced_ran ? F_FORCED_RAN : 0) |
-                                          (out_forced ? F_FROM_FORCED : 0));
-            if (a.iters) a.iters[shot] = (int16_t)t;
-            acc_it += (unsigned long long)t;
-            acc_msg += (unsigned long long)s * s * t;
-            acc_def += (unsigned long long)s;
-            acc_shots += 1;
-        }
-        __syncthreads();
-    }
-    if (tid == 0 && a.ctr) {
-        atomicAdd(a.ctr + C_ITERS, acc_it);
-        atomicAdd(a.ctr + C_MSGS, acc_msg);
-        atomicAdd(a.ctr + C_DEFECTS, acc_def);
-        atomicAdd(a.ctr + C_TIER_MSGS + a.tier, acc_msg);
-        atomicAdd(a.ctr + C_TIER_SHOTS + a.tier, acc_shots);
-        atomicAdd(a.ctr + C_FC_RUNS, acc_fc);
-        atomicAdd(a.ctr + C_FC_ROUNDS, acc_fcr);
-    }
-}
 
 // ------------------------------------------------------------------ global-memory tier
 //
@@ -1179,28 +657,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;
 std::atomic<void*> g_noalloc_addr[kMaxDevices];
-
-// ------------------------------------------------------------------ tier table
-
-struct TierCfg {
-    int smax;
-    int ch, g;
-};
-
-// FP32: 32/64/96/128/160 rows in shared memory; FP64: 32/64/112 (tiers 4, 5 unused).
-constexpr TierCfg kCfg32[6] = {{0, 0, 0}, {32, 32, 1}, {64, 32, 2}, {96, 24, 4}, {128, 32, 4}, {160, 40, 4}};
-constexpr TierCfg kCfg64[6] = {{0, 0, 0}, {32, 16, 2}, {64, 16, 4}, {112, 28, 4}, {112, 28, 4}, {112, 28, 4}};
-// FP32 tiers that keep their own outputs in registers (the 96- and 160-row tiers have no
-// register room for them).
-constexpr bool kReg32[6] = {false, true, true, false, true, false};
-
-template <typename T, int CH, int G>
-size_t smem_bytes_of() {
-    constexpr int SMAX = CH * G;
-    constexpr int P = pitch_of<T>(SMAX, G);
-    return (size_t)(2 * SMAX * P + SMAX + (SMAX & 1)) * sizeof(T) +
-           (size_t)SMAX * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 16;
-}
 
 template <typename T, int CH, int G, bool TRACE, bool REG>
 cudaError_t run_tier(const DecodeArgs& a, int num_sms, cudaStream_t st, bool prepare_only) {

@@ -131,7 +131,8 @@ constexpr int kClsThreads = 256;
 __global__ void __launch_bounds__(kClsThreads) classify_kernel(
     const uint32_t* __restrict__ synd, int64_t shots, int n_words, TierPlan plan,
     int32_t* lists, int32_t* counts, int32_t* max_s, uint8_t* obs_pred, uint8_t* flags,
-    int16_t* iters, int32_t* tr_defects) {
+    int16_t* iters, int32_t* tr_defects, const uint8_t* skip, const uint8_t* skip_obs,
+    const int16_t* skip_iters) {
     int local_max = 0;
     for (int64_t shot = (int64_t)blockIdx.x * kClsThreads + threadIdx.x; shot < shots;
          shot += (int64_t)gridDim.x * kClsThreads) {
@@ -139,6 +140,12 @@ __global__ void __launch_bounds__(kClsThreads) classify_kernel(
         int s = 0;
         for (int k = 0; k < n_words; ++k) s += __popc(__ldg(w + k));
         if (tr_defects) tr_defects[shot] = s;
+        if (skip && skip[shot]) {
+            if (obs_pred) obs_pred[shot] = skip_obs[shot];
+            if (flags) flags[shot] = F_CONVERGED | F_FROM_QBP;
+            if (iters) iters[shot] = skip_iters[shot];
+            continue;
+        }
         local_max = max(local_max, s);
         if (s == 0) {
             if (obs_pred) obs_pred[shot] = 0;
@@ -224,10 +231,12 @@ cudaError_t launch_sample_code_capacity(const SampleArgs& a, cudaStream_t st) {
 
 cudaError_t launch_classify(const uint32_t* synd, int64_t shots, int n_words, const TierPlan& plan,
                             int32_t* lists, int32_t* counts, int32_t* max_s, uint8_t* obs_pred,
-                            uint8_t* flags, int16_t* iters, int32_t* tr_defects, cudaStream_t st) {
+                            uint8_t* flags, int16_t* iters, int32_t* tr_defects, const uint8_t* skip,
+                            const uint8_t* skip_obs, const int16_t* skip_iters, cudaStream_t st) {
     if (shots <= 0) return cudaSuccess;
     classify_kernel<<<grid_for(shots, kClsThreads, 152 * 8), kClsThreads, 0, st>>>(
-        synd, shots, n_words, plan, lists, counts, max_s, obs_pred, flags, iters, tr_defects);
+        synd, shots, n_words, plan, lists, counts, max_s, obs_pred, flags, iters, tr_defects, skip,
+        skip_obs, skip_iters);
     return cudaGetLastError();
 }
 

@@ -288,3 +288,40 @@ def test_unrotated_sampler_and_decoding(torch):
         n_det = gc.info()["n_det"][ty]
         assert np.array_equal(as_bool(synds[ty], n_det), ref[kind][0])
         assert np.array_equal(obsc[ty].cpu().numpy(), ref[kind][1])
+
+
+# ------------------------------------------------------------------ B-BP4MF
+
+
+# (precision, d, p, shots, minimum agreement): d = 5 covers the smallest tiers; d = 17 at
+# p = 0.15 gives 60-100 unsatisfied checks per type (FP64 tiers 2-3), d = 21 at p = 0.155
+# about 130 (FP32 tiers 4-5)
+BBP_CASES = [("fp64", 5, 0.1, 300, 0.99), ("fp32", 5, 0.1, 300, 0.97),
+             ("fp64", 17, 0.15, 12, 0.9), ("fp32", 21, 0.155, 8, 0.85)]
+
+
+@pytest.mark.parametrize("prec,d,p,n,min_agree", BBP_CASES)
+def test_bbp4mf_matches_oracle(torch, prec, d, p, n, min_agree):
+    from oracle.bbp4mf import bbp4mf_shot
+    from oracle.surface import unrotated_code
+    T = 25
+    g = pkg.Graph(d, "code_capacity", p, family="unrotated")
+    info = g.info()
+    synds, obs = gpu_sample(g, 0, n, seed=17)
+    flat = torch.cat([synds[0].reshape(-1), synds[1].reshape(-1)]).contiguous()
+    pred = torch.empty((2, n), dtype=torch.uint8, device="cuda")
+    flags = torch.empty((2, n), dtype=torch.uint8, device="cuda")
+    g.decode_bbp4mf(flat, T, pkg.make_opts(precision=prec), pred, flags)
+    torch.cuda.synchronize()
+    pred, flags = pred.cpu().numpy(), flags.cpu().numpy()
+    code = unrotated_code(d)
+    graphs = {k: code_capacity_graph(code, k) for k in ("X", "Z")}
+    sz = as_bool(synds[0], info["n_det"][0])   # Z-checks
+    sx = as_bool(synds[1], info["n_det"][1])   # X-checks
+    agree = stage = 0
+    for k in range(n):
+        out = bbp4mf_shot(code, graphs, sx[k].astype(int), sz[k].astype(int), p, T, T)
+        agree += int(out["X"] == pred[0, k] and out["Z"] == pred[1, k])
+        stage += int(bool(out["qbp_converged"]) == bool(flags[0, k] & 8))
+    print("B-BP4MF %s d=%d p=%.3f: %d/%d shots agree, first stage agrees on %d" % (prec, d, p, agree, n, stage))
+    assert agree >= min_agree * n and stage >= min_agree * n

@@ -62,3 +62,24 @@ def test_bbp4mf_corrects_every_weight_one_error_d3(family):
             out = bbp4mf_shot(code, graphs, sx, sz, 0.05, 25, 25)
             assert out["X"] == int(ex[code.zl].sum() % 2)
             assert out["Z"] == int(ez[code.xl].sum() % 2)
+
+
+def test_reweighting_floors_weights_of_likely_errors():
+    # posteriors at or above one half would make edges free or negative; the floor keeps
+    # every shortest path well defined and every prior finite, and a path over k floored
+    # edges weighs exactly k * 2^-20
+    from oracle.bbp4mf import MIN_WEIGHT
+    code = make_code(5)
+    g = code_capacity_graph(code, "X")
+    probs = [0.9 if e % 3 == 0 else 0.5 for e in range(len(g.edges))]
+    dets = np.arange(g.n_det)
+    W, P, L = reweighted_tables(g, probs, dets)
+    assert np.isfinite(L).all() and (W > 0).all()
+    # every edge floored: W counts hops of the shortest path
+    W1, _, _ = reweighted_tables(g, [0.75] * len(g.edges), dets)
+    hops = np.rint(W1 / MIN_WEIGHT)
+    assert np.allclose(W1, hops * MIN_WEIGHT, rtol=1e-12) and (hops >= 1).all()
+    # neighbouring checks of one qubit are one hop apart
+    u, v = g.edges[0][0], g.edges[0][1]
+    if v < g.n_det:
+        assert hops[u, v] == 1
