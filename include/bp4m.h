@@ -227,9 +227,9 @@ int bp4m_decode_noalloc(const bp4m_graph* g, const uint32_t* syndromes, int64_t 
    this graph is bracketed by CUDA events recorded on the launch stream, and the
    algorithmic message updates of each decoding tier are counted.  Enabling resets the
    accumulators; reading synchronises the events.  Slots: 0 = defect classification,
-   1..5 = shared-memory decode tiers (s <= 32, 64, 96, 128, 160 in FP32; 32, 64, 112 in
-   FP64), 6 = global-memory decode tier, 7 = sampler, 8 = failure counting. */
-#define BP4M_PROF_SLOTS 9
+   1..7 = shared-memory decode tiers (s <= 32, 64, 96, 112, 128, 144, 160 in FP32; 32, 64,
+   112 in FP64), 8 = global-memory decode tier, 9 = sampler, 10 = failure counting. */
+#define BP4M_PROF_SLOTS 11
 typedef struct {
     int64_t launches[BP4M_PROF_SLOTS];
     double ms[BP4M_PROF_SLOTS];                /* summed event-timed durations */

@@ -146,7 +146,7 @@ class Graph:
         check(load().bp4m_profile_enable(self._h, 1 if on else 0))
 
     def profile_read(self):
-        """Per slot (classify, tier1..4, global, sample, count): launches, ms, msg updates, shots."""
+        """Per slot (classify, tier1..7, global, sample, count): launches, ms, msg updates, shots."""
         pr = _capi.Profile()
         check(load().bp4m_profile_read(self._h, ctypes.byref(pr)))
         return {name: {"launches": pr.launches[k], "ms": pr.ms[k], "msg_updates": pr.msg_updates[k],

@@ -60,11 +60,12 @@ class Edge(ctypes.Structure):
 
 
 class Profile(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 9), ("ms", ctypes.c_double * 9),
-                ("msg_updates", ctypes.c_uint64 * 9), ("shots", ctypes.c_uint64 * 9)]
+    _fields_ = [("launches", ctypes.c_int64 * 11), ("ms", ctypes.c_double * 11),
+                ("msg_updates", ctypes.c_uint64 * 11), ("shots", ctypes.c_uint64 * 11)]
 
 
-PROFILE_SLOTS = ["classify", "tier1", "tier2", "tier3", "tier4", "tier5", "global", "sample", "count"]
+PROFILE_SLOTS = ["classify", "tier1", "tier2", "tier3", "tier4", "tier5", "tier6", "tier7", "global", "sample",
+                 "count"]
 
 
 class Trace(ctypes.Structure):

@@ -122,7 +122,8 @@ namespace {
 
 int n_words_of(const bp4m_graph* g, int ty) { return (g->host.t[ty].n_det + 31) / 32; }
 
-enum { PROF_CLASSIFY = 0, PROF_GLOBAL = 6, PROF_SAMPLE = 7, PROF_COUNT = 8 };
+enum { PROF_CLASSIFY = 0, PROF_GLOBAL = kGlobalTier, PROF_SAMPLE = kGlobalTier + 1, PROF_COUNT = kGlobalTier + 2 };
+static_assert(PROF_COUNT + 1 == BP4M_PROF_SLOTS, "profile slots");
 
 // Brackets one kernel launch with events when profiling is on.
 struct ProfScope {

@@ -125,11 +125,49 @@ struct B2<double> {
 constexpr double kLog2e = 1.4426950408889634074;
 constexpr double kLn2 = 0.69314718055994530942;
 
-// Row pitch in elements.  FP32: pitch = G (mod 32) makes a warp's row reads (R rows x G
-// column groups) hit 32 distinct banks; column accesses are at most 2-way.  FP64: +1.
+// Row pitch in elements.  FP32: pitch = G x odd, the smallest such value >= smax: the R
+// rows a warp reads (R x G = 32) then start at R distinct multiples of G modulo 32, so the
+// warp's row reads hit 32 distinct banks; column accesses are at most 2-way.  FP64: +1.
 template <typename T>
 __host__ __device__ constexpr int pitch_of(int smax, int g) {
-    return sizeof(T) == 8 ? smax + 1 : smax + ((g - smax % 32) % 32 + 32) % 32;
+    return sizeof(T) == 8 ? smax + 1 : g * (((smax + g - 1) / g) | 1);
+}
+
+// A thread's register-cached row entries (CH columns).  FP32 keeps them as float2 pairs,
+// columns (2j, 2j+1) in one 64-bit register pair, so that the packed FP32x2 add and FMA of
+// sm_100 and later apply to two columns per instruction.
+template <typename T, int N>
+struct Regs {
+    T v[N];
+    __device__ __forceinline__ T& operator[](int c) { return v[c]; }
+    // runtime column index: a select chain, so that the array stays in registers
+    __device__ __forceinline__ T get(int c) const {
+        T r = T(0);
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            if (k == c) r = v[k];
+        return r;
+    }
+};
+
+template <int N>
+struct Regs<float, N> {
+    static_assert(N % 2 == 0, "FP32 rows are cached in column pairs");
+    float2 p[N / 2];
+    __device__ __forceinline__ float& operator[](int c) { return (c & 1) ? p[c >> 1].y : p[c >> 1].x; }
+    __device__ __forceinline__ float get(int c) const {
+        float r = 0.f;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            if (k == c) r = (k & 1) ? p[k >> 1].y : p[k >> 1].x;
+        return r;
+    }
+};
+
+__device__ __forceinline__ float max3f(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
 
 // (max, second max, column of the max) of two partial row scans; ties go to the smaller
@@ -145,9 +183,12 @@ __device__ __forceinline__ void combine_max(T& m1, T& m2, int& k, T o1, T o2, in
     }
 }
 
-// Blocks per SM the kernel is compiled for: the 384-thread tier (96 rows, 79 KB of shared
-// memory) runs two blocks per SM; the others are limited by shared memory or 128 registers.
-__host__ __device__ constexpr int blocks_for(int nt) { return nt == 384 ? 2 : min_blocks(nt); }
+// Blocks per SM the kernel is compiled for: the FP32 384- and 448-thread tiers (96 and 112
+// rows, 79 and 106 KB of shared memory) run two blocks per SM; the others are limited by
+// shared memory or 128 registers.
+__host__ __device__ constexpr int blocks_for(int nt, int elem_bytes) {
+    return (elem_bytes == 4 && (nt == 384 || nt == 448)) ? 2 : min_blocks(nt);
+}
 
 // REG = true keeps each thread's own outputs M[i][k] in registers between iterations (no
 // strided shared-memory read per message); REG = false reads them back from Mt[k][i].
@@ -155,7 +196,7 @@ __host__ __device__ constexpr int blocks_for(int nt) { return nt == 384 ? 2 : mi
 // computed in the block by Dijkstra from every defect over per-qubit weights derived from
 // the first stage's posteriors (instead of being gathered from the static tables).
 template <typename T, int CH, int G, bool TRACE, bool REG, bool RW = false>
-__global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G)) decode_smem_kernel(const DecodeArgs a) {
+__global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof(T))) decode_smem_kernel(const DecodeArgs a) {
     constexpr int SMAX = CH * G;
     constexpr int NT = SMAX * G;
     constexpr int R = 32 / G;
@@ -358,8 +399,11 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G)) decode_sme
         }
 
         const bool act = i < s;
-        T q[CH];
-        T mo[REG ? CH : 1];
+        // rows warp*R .. warp*R+R-1 belong to this warp; a warp with none of them active
+        // skips the read and compute phases (it still takes part in every barrier)
+        const bool wact = warp * R < s;
+        Regs<T, CH> q;
+        Regs<T, REG ? CH : 2> mo;
         int am_prev = -1;          // REG: argmax column of the previous update and its output
         T out_am = T(0);
         int t = 0;
@@ -371,13 +415,57 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G)) decode_sme
             // ---- read phase: Q = l + M[k][i]/alpha for the next update; for t > 0 the
             // marginalization of lambda^t = l + (M[i][k] + M[k][i])
             Mask bits = 0;
-            if (!act) {
+            if (!wact) {
+            } else if (!act) {
 #pragma unroll
                 for (int c = 0; c < CH; ++c) q[c] = ninf;
             } else {
                 if (t == 0) {
+                    if constexpr (std::is_same<T, float>::value) {
+                        const float2 ainv2 = make_float2(ainv, ainv);
 #pragma unroll
-                    for (int c = 0; c < CH; ++c) q[c] = B2<T>::fma_(row_m[G * c], ainv, row_l[G * c]);
+                        for (int j = 0; j < CH / 2; ++j)
+                            q.p[j] = __ffma2_rn(make_float2(row_m[G * 2 * j], row_m[G * (2 * j + 1)]), ainv2,
+                                                make_float2(row_l[G * 2 * j], row_l[G * (2 * j + 1)]));
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < CH; ++c) q[c] = B2<T>::fma_(row_m[G * c], ainv, row_l[G * c]);
+                    }
+                } else if constexpr (std::is_same<T, float>::value) {
+                    // two columns per packed instruction; same roundings as the scalar form
+                    const float2 ainv2 = make_float2(ainv, ainv);
+                    Mask b0 = 0, b1 = 0;
+#pragma unroll
+                    for (int j = 0; j < CH / 2; ++j) {
+                        const int c = 2 * j;
+                        const float2 l = make_float2(row_l[G * c], row_l[G * (c + 1)]);
+                        const float2 x = make_float2(row_m[G * c], row_m[G * (c + 1)]);
+                        float2 own;
+                        if constexpr (REG)
+                            own = mo.p[j];
+                        else
+                            own = make_float2(col_m[G * P * c], col_m[G * P * (c + 1)]);
+                        q.p[j] = __ffma2_rn(x, ainv2, l);
+                        const float2 lam = __fadd2_rn(l, __fadd2_rn(own, x));
+                        b0 |= (Mask)(lam.x > 0.f ? 1u : 0u) << c;
+                        b1 |= (Mask)(lam.y > 0.f ? 1u : 0u) << (c + 1);
+                        if (tr_on && trl && g + G * c < s)
+                            trl[((size_t)shot * a.s_cap + i) * a.s_cap + g + G * c] = lam.x * (float)kLn2;
+                        if (tr_on && trl && g + G * (c + 1) < s)
+                            trl[((size_t)shot * a.s_cap + i) * a.s_cap + g + G * (c + 1)] = lam.y * (float)kLn2;
+                    }
+                    bits = b0 | b1;
+                    if (!REG && own_diag) {
+                        const float lam = Lm[i * P + i] + Dg[i];
+                        bits = (bits & ~((Mask)1 << c_diag)) | ((Mask)(lam > 0.f ? 1u : 0u) << c_diag);
+                        if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + i] = lam * (float)kLn2;
+                    }
+                    if (REG && am_prev % G == g) {
+                        const int ca = am_prev / G;
+                        const float lam = Lm[i * P + am_prev] + (out_am + Mt[i * P + am_prev]);
+                        bits = (bits & ~((Mask)1 << ca)) | ((Mask)(lam > 0.f ? 1u : 0u) << ca);
+                        if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + am_prev] = lam * (float)kLn2;
+                    }
                 } else {
                     Mask b0 = 0, b1 = 0;
 #pragma unroll
@@ -431,7 +519,7 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G)) decode_sme
                     forced_ran = true;
                     if (act && g == 0) matched[i] = 0;
                     __syncthreads();
-                    const T lii = act ? (REG ? Lm[i * P + i] + (mo[REG ? c_diag : 0] + T(0)) : Lm[i * P + i] + Dg[i]) : ninf;
+                    const T lii = act ? (REG ? Lm[i * P + i] + (mo.get(c_diag) + T(0)) : Lm[i * P + i] + Dg[i]) : ninf;
                     for (int round = 0; round < s; ++round) {
                         const bool open = act && !matched[i];
                         T bl = ninf;
@@ -546,30 +634,53 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G)) decode_sme
             // (the max clamped to m2, so S - 1 = sum_{k != am} 2^(Q_k - m2) >= 1):
             //   k != am: M'[i][k] = -(m1 + lg2(1 + 2^(m2 - m1) (S - 1 - 2^(Q_k - m2))))
             //   k == am: M'[i][k] = -(m2 + lg2(S - 1))
-            {
-                T a1 = ninf, a2 = ninf, b1 = ninf, b2 = ninf;
-                int ac = 0x7fffffff, bc = 0x7fffffff;
+            if (wact) {
+                T m1, m2;
+                int am;
+                if constexpr (std::is_same<T, float>::value) {
+                    // column pairs: hi/lo of the pair, then the running (max, second max);
+                    // ties go to the smaller column
+                    float a1 = ninf, a2 = ninf;
+                    int ac = 0x7fffffff;
 #pragma unroll
-                for (int c = 0; c < CH; c += 2) {
-                    const T v = q[c];
-                    const bool gt = v > a1;
-                    a2 = B2<T>::mx(a2, B2<T>::mn(v, a1));
-                    a1 = B2<T>::mx(a1, v);
-                    ac = gt ? c : ac;
-                    if (c + 1 < CH) {
-                        const T w = q[c + 1];
-                        const bool gw = w > b1;
-                        b2 = B2<T>::mx(b2, B2<T>::mn(w, b1));
-                        b1 = B2<T>::mx(b1, w);
-                        bc = gw ? c + 1 : bc;
+                    for (int j = 0; j < CH / 2; ++j) {
+                        const float v = q.p[j].x, w = q.p[j].y;
+                        const float hi = fmaxf(v, w), lo = fminf(v, w);
+                        const int ih = v >= w ? 2 * j : 2 * j + 1;
+                        const bool gt = hi > a1;
+                        a2 = max3f(a2, lo, fminf(a1, hi));
+                        a1 = fmaxf(a1, hi);
+                        ac = gt ? ih : ac;
                     }
+                    m1 = a1;
+                    m2 = a2;
+                    am = ac < CH ? g + G * ac : 0x7fffffff;
+                } else {
+                    T a1 = ninf, a2 = ninf, b1 = ninf, b2 = ninf;
+                    int ac = 0x7fffffff, bc = 0x7fffffff;
+#pragma unroll
+                    for (int c = 0; c < CH; c += 2) {
+                        const T v = q[c];
+                        const bool gt = v > a1;
+                        a2 = B2<T>::mx(a2, B2<T>::mn(v, a1));
+                        a1 = B2<T>::mx(a1, v);
+                        ac = gt ? c : ac;
+                        if (c + 1 < CH) {
+                            const T w = q[c + 1];
+                            const bool gw = w > b1;
+                            b2 = B2<T>::mx(b2, B2<T>::mn(w, b1));
+                            b1 = B2<T>::mx(b1, w);
+                            bc = gw ? c + 1 : bc;
+                        }
+                    }
+                    // column indices of the two partial maxima (ties to the smaller column)
+                    int ka = ac < CH ? g + G * ac : 0x7fffffff;
+                    int kb = bc < CH ? g + G * bc : 0x7fffffff;
+                    combine_max(a1, a2, ka, b1, b2, kb);
+                    m1 = a1;
+                    m2 = a2;
+                    am = ka;
                 }
-                // column indices of the two partial maxima (ties to the smaller column)
-                int ka = ac < CH ? g + G * ac : 0x7fffffff;
-                int kb = bc < CH ? g + G * bc : 0x7fffffff;
-                combine_max(a1, a2, ka, b1, b2, kb);
-                T m1 = a1, m2 = a2;
-                int am = ka;
 #pragma unroll
                 for (int off = R; off < 32; off <<= 1) {
                     const T o1 = __shfl_xor_sync(kFull, m1, off);
@@ -577,29 +688,58 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G)) decode_sme
                     const int ok = __shfl_xor_sync(kFull, am, off);
                     combine_max(m1, m2, am, o1, o2, ok);
                 }
-                T sa = T(0), sb = T(0);
+                T S;
+                if constexpr (std::is_same<T, float>::value) {
+                    const float2 nm2 = make_float2(-m2, -m2);
+                    float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int c = 0; c < CH; c += 2) {
-                    const T u = B2<T>::ex2(B2<T>::mn(q[c], m2) - m2);
-                    q[c] = u;
-                    sa += u;
-                    if (c + 1 < CH) {
-                        const T w = B2<T>::ex2(B2<T>::mn(q[c + 1], m2) - m2);
-                        q[c + 1] = w;
-                        sb += w;
+                    for (int j = 0; j < CH / 2; ++j) {
+                        const float2 dq = __fadd2_rn(make_float2(fminf(q.p[j].x, m2), fminf(q.p[j].y, m2)), nm2);
+                        const float2 u = make_float2(B2<float>::ex2(dq.x), B2<float>::ex2(dq.y));
+                        q.p[j] = u;
+                        s2 = __fadd2_rn(s2, u);
                     }
+                    S = s2.x + s2.y;
+                } else {
+                    T sa = T(0), sb = T(0);
+#pragma unroll
+                    for (int c = 0; c < CH; c += 2) {
+                        const T u = B2<T>::ex2(B2<T>::mn(q[c], m2) - m2);
+                        q[c] = u;
+                        sa += u;
+                        if (c + 1 < CH) {
+                            const T w = B2<T>::ex2(B2<T>::mn(q[c + 1], m2) - m2);
+                            q[c + 1] = w;
+                            sb += w;
+                        }
+                    }
+                    S = sa + sb;
                 }
-                T S = sa + sb;
 #pragma unroll
                 for (int off = R; off < 32; off <<= 1) S += __shfl_xor_sync(kFull, S, off);
                 const T cf = B2<T>::ex2(m2 - m1);
                 const T Aa = B2<T>::fma_(cf, S - T(1), T(1));
                 if (act) {
+                    if constexpr (std::is_same<T, float>::value) {
+                        // out = -m1 - lg2(Aa - cf u), the subtraction as an exact fma with -1
+                        const float2 ncf = make_float2(-cf, -cf), A2 = make_float2(Aa, Aa);
+                        const float2 nm1 = make_float2(-m1, -m1), neg1 = make_float2(-1.f, -1.f);
 #pragma unroll
-                    for (int c = 0; c < CH; ++c) {
-                        const T out = -m1 - B2<T>::lg2(B2<T>::fma_(-cf, q[c], Aa));
-                        col_m[G * P * c] = out;
-                        if (REG) mo[REG ? c : 0] = out;
+                        for (int j = 0; j < CH / 2; ++j) {
+                            const float2 y = __ffma2_rn(ncf, q.p[j], A2);
+                            const float2 lg = make_float2(B2<float>::lg2(y.x), B2<float>::lg2(y.y));
+                            const float2 out = __ffma2_rn(lg, neg1, nm1);
+                            col_m[G * P * 2 * j] = out.x;
+                            col_m[G * P * (2 * j + 1)] = out.y;
+                            if constexpr (REG) mo.p[j] = out;
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < CH; ++c) {
+                            const T out = -m1 - B2<T>::lg2(B2<T>::fma_(-cf, q[c], Aa));
+                            col_m[G * P * c] = out;
+                            if (REG) mo[REG ? c : 0] = out;
+                        }
                     }
                     const T oam = -m2 - B2<T>::lg2(S - T(1));
                     if (am % G == g) Mt[am * P + i] = oam;
@@ -656,12 +796,16 @@ struct TierCfg {
     int ch, g;
 };
 
-// FP32: 32/64/96/128/160 rows in shared memory; FP64: 32/64/112 (tiers 4, 5 unused).
-constexpr TierCfg kCfg32[6] = {{0, 0, 0}, {32, 32, 1}, {64, 32, 2}, {96, 24, 4}, {128, 32, 4}, {160, 40, 4}};
-constexpr TierCfg kCfg64[6] = {{0, 0, 0}, {32, 16, 2}, {64, 16, 4}, {112, 28, 4}, {112, 28, 4}, {112, 28, 4}};
-// FP32 tiers that keep their own outputs in registers (the 96- and 160-row tiers have no
-// register room for them).
-constexpr bool kReg32[6] = {false, true, true, false, true, false};
+// FP32: 32/64/96/112/128/144/160 rows in shared memory; FP64: 32/64/112 (tiers 4..7
+// unused).  The 16-row steps from 96 rows up follow the defect counts of circuit-level
+// shots (d = 13, p = 0.005: s = 126 +- 16), where padding rows and columns cost issue slots.
+constexpr int kSmemTiers = 7;
+constexpr TierCfg kCfg32[kSmemTiers + 1] = {{0, 0, 0},     {32, 32, 1},  {64, 32, 2},  {96, 24, 4},
+                                            {112, 28, 4}, {128, 32, 4}, {144, 36, 4}, {160, 40, 4}};
+constexpr TierCfg kCfg64[kSmemTiers + 1] = {{0, 0, 0},     {32, 16, 2},  {64, 16, 4},  {112, 28, 4},
+                                            {112, 28, 4}, {112, 28, 4}, {112, 28, 4}, {112, 28, 4}};
+// FP32 tiers that keep their own outputs in registers (the others have no register room).
+constexpr bool kReg32[kSmemTiers + 1] = {false, true, true, false, false, true, false, false};
 
 // Bytes of one RW scratch slot: W [SMAX][SMAX] doubles, Dijkstra distances [warps][nodes]
 // doubles, parity [SMAX][SMAX] bytes, done and parity flags [warps][nodes] bytes.

@@ -25,9 +25,9 @@ enum CounterSlot {
     C_CONVFAIL_X, C_CONVFAIL_Z,
     C_ITERS, C_MSGS, C_DEFECTS,
     C_ERRORS,          // shots the kernels refused (internal consistency checks)
-    C_TIER_MSGS,       // 7 slots: message updates per decode tier
-    C_TIER_SHOTS = C_TIER_MSGS + 7,  // 7 slots: shots per decode tier
-    C_FC_RUNS = C_TIER_SHOTS + 7,    // forced-convergence runs
+    C_TIER_MSGS,       // 9 slots: message updates per decode tier
+    C_TIER_SHOTS = C_TIER_MSGS + 9,  // 9 slots: shots per decode tier
+    C_FC_RUNS = C_TIER_SHOTS + 9,    // forced-convergence runs
     C_FC_ROUNDS,                     // locally-dominant rounds summed over runs
     C_UNCONV_ANY,                    // shots with at least one unconverged type
     C_CONVFAIL_ANY,                  // shots with every type converged and some type failed
@@ -38,8 +38,8 @@ enum CounterSlot {
 enum : uint8_t { F_CONVERGED = 1, F_FORCED_RAN = 2, F_FROM_FORCED = 4, F_FROM_QBP = 8 };
 
 // Number of s tiers and the per-tier bookkeeping in the workspace.
-constexpr int kTiers = 7;      // tier 0: s == 0 (done in classify), 1..5 shared memory, 6 global
-constexpr int kGlobalTier = 6;
+constexpr int kTiers = 9;      // tier 0: s == 0 (done in classify), 1..7 shared memory, 8 global
+constexpr int kGlobalTier = 8;
 
 struct TierPlan {
     int smax[kTiers];  // inclusive upper bound of s for the tier (global tier: unbounded)
@@ -143,19 +143,19 @@ cudaError_t launch_classify(const uint32_t* synd, int64_t shots, int n_words,
                             int16_t* iters, int32_t* tr_defects, const uint8_t* skip,
                             const uint8_t* skip_obs, const int16_t* skip_iters, cudaStream_t st);
 
-// Launch the decoding kernel of shared-memory tier `tier` (1..5) for precision
+// Launch the decoding kernel of shared-memory tier `tier` (1..7) for precision
 // (0 = FP64, 1 = FP32).  Returns cudaSuccess if the tier is empty by construction.
 cudaError_t launch_decode_tier(int precision, int tier, const DecodeArgs& a, int num_sms,
                                cudaStream_t st);
-// Reweighting (B-BP4MF second stage) decode of the shared-memory tiers (FP32 1..5, FP64
+// Reweighting (B-BP4MF second stage) decode of the shared-memory tiers (FP32 1..7, FP64
 // 1..3).  rw_scratch_bytes() is the global scratch the launch of `tier` needs for a graph
 // of n_det detectors (one slot per resident block) and sets *slot_bytes; the caller
 // passes that scratch in a.gscratch and the slot size in a.rw_slot_bytes.
 size_t rw_scratch_bytes(int precision, int tier, int n_det, int num_sms, int64_t* slot_bytes);
 cudaError_t launch_decode_tier_rw(int precision, int tier, const DecodeArgs& a, int num_sms,
                                   cudaStream_t st);
-// Highest shared-memory tier per precision (FP64 tiers 4 and 5 are never populated).
-constexpr int kRwMaxTier32 = 5;
+// Highest shared-memory tier per precision (FP64 tiers 4..7 are never populated).
+constexpr int kRwMaxTier32 = 7;
 constexpr int kRwMaxTier64 = 3;
 // Smallest edge weight of the reweighted graph: posteriors at or above one half would give
 // weights <= 0, for which shortest paths do not exist on an undirected graph.

@@ -693,8 +693,10 @@ cudaError_t dispatch_tier<float>(int tier, const DecodeArgs& a, int num_sms, cud
         case 1: return run_tier2<float, 32, 1, kReg32[1]>(a, num_sms, st, prep);
         case 2: return run_tier2<float, 32, 2, kReg32[2]>(a, num_sms, st, prep);
         case 3: return run_tier2<float, 24, 4, kReg32[3]>(a, num_sms, st, prep);
-        case 4: return run_tier2<float, 32, 4, kReg32[4]>(a, num_sms, st, prep);
-        case 5: return run_tier2<float, 40, 4, kReg32[5]>(a, num_sms, st, prep);
+        case 4: return run_tier2<float, 28, 4, kReg32[4]>(a, num_sms, st, prep);
+        case 5: return run_tier2<float, 32, 4, kReg32[5]>(a, num_sms, st, prep);
+        case 6: return run_tier2<float, 36, 4, kReg32[6]>(a, num_sms, st, prep);
+        case 7: return run_tier2<float, 40, 4, kReg32[7]>(a, num_sms, st, prep);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -705,7 +707,7 @@ cudaError_t dispatch_tier<double>(int tier, const DecodeArgs& a, int num_sms, cu
         case 1: return run_tier2<double, 16, 2, false>(a, num_sms, st, prep);
         case 2: return run_tier2<double, 16, 4, false>(a, num_sms, st, prep);
         case 3: return run_tier2<double, 28, 4, false>(a, num_sms, st, prep);
-        case 4: case 5: return cudaSuccess;  // same bound as tier 3: never populated
+        case 4: case 5: case 6: case 7: return cudaSuccess;  // same bound as tier 3: never populated
         default: return cudaErrorInvalidValue;
     }
 }

@@ -62,8 +62,10 @@ cudaError_t dispatch_rw(int precision, int tier, const DecodeArgs& a, int num_sm
         case 1: return run_tier_rw<float, 32, 1, kReg32[1]>(a, num_sms, st, query);
         case 2: return run_tier_rw<float, 32, 2, kReg32[2]>(a, num_sms, st, query);
         case 3: return run_tier_rw<float, 24, 4, kReg32[3]>(a, num_sms, st, query);
-        case 4: return run_tier_rw<float, 32, 4, kReg32[4]>(a, num_sms, st, query);
-        case 5: return run_tier_rw<float, 40, 4, kReg32[5]>(a, num_sms, st, query);
+        case 4: return run_tier_rw<float, 28, 4, kReg32[4]>(a, num_sms, st, query);
+        case 5: return run_tier_rw<float, 32, 4, kReg32[5]>(a, num_sms, st, query);
+        case 6: return run_tier_rw<float, 36, 4, kReg32[6]>(a, num_sms, st, query);
+        case 7: return run_tier_rw<float, 40, 4, kReg32[7]>(a, num_sms, st, query);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -202,7 +202,7 @@ def _random_syndromes(n_det, sizes, seed):
 def test_every_tier_boundary_d13(torch, prec, early):
     # defect counts on both sides of every shared-memory tier bound and in the global tier
     g, og, ot = circuit_pair(13, 0.005)
-    sizes = [0, 1, 2, 3, 31, 32, 33, 63, 64, 65, 95, 96, 97, 111, 112, 113, 127, 128, 129, 159, 160,
+    sizes = [0, 1, 2, 3, 31, 32, 33, 63, 64, 65, 95, 96, 97, 111, 112, 113, 127, 128, 129, 143, 144, 145, 159, 160,
              161, 200, 256, 257, 300]
     sb = _random_syndromes(og.n_det, sizes, seed=17 + early)
     synd = torch.as_tensor(pack_syndromes(sb).view(np.int32), device="cuda")
@@ -295,7 +295,7 @@ def test_unrotated_sampler_and_decoding(torch):
 
 # (precision, d, p, shots, minimum agreement): d = 5 covers the smallest tiers; d = 17 at
 # p = 0.15 gives 60-100 unsatisfied checks per type (FP64 tiers 2-3), d = 21 at p = 0.155
-# about 130 (FP32 tiers 4-5)
+# about 130 (FP32 tiers 5-7)
 BBP_CASES = [("fp64", 5, 0.1, 300, 0.99), ("fp32", 5, 0.1, 300, 0.97),
              ("fp64", 17, 0.15, 12, 0.9), ("fp32", 21, 0.155, 8, 0.85)]
 
