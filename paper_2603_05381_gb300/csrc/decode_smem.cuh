@@ -22,7 +22,7 @@
 //
 // Layout (shared-memory tiers): Mt[i][k] = M[k][i], the message arriving at factor i from
 // the factor k side; Lm[i][k] = l_ik.  Row i is processed by G threads, thread g taking
-// columns k = g + G*c.  The update is in place: every thread caches its row in registers,
+// the columns of col_off() (FP32: adjacent pairs 2g, 2g+1, then every 2G; FP64: g + G*c).  The update is in place: every thread caches its row in registers,
 // the block synchronises, then each thread writes its outputs M'[i][k] into Mt[k][i].
 #include <cuda_runtime.h>
 
@@ -125,12 +125,31 @@ struct B2<double> {
 constexpr double kLog2e = 1.4426950408889634074;
 constexpr double kLn2 = 0.69314718055994530942;
 
-// Row pitch in elements.  FP32: pitch = G x odd, the smallest such value >= smax: the R
-// rows a warp reads (R x G = 32) then start at R distinct multiples of G modulo 32, so the
-// warp's row reads hit 32 distinct banks; column accesses are at most 2-way.  FP64: +1.
+// Column ownership.  FP32 (PAIR): thread g of a row owns adjacent column pairs, its
+// register c holding column k0 + col_off(c) with k0 = 2g and col_off(c) = (c & 1) +
+// 2G (c >> 1), so that one 64-bit shared load fetches both columns of a pair.  FP64:
+// k0 = g, col_off(c) = G c.
+template <bool PAIR, int G>
+__host__ __device__ constexpr int col_off(int c) {
+    return PAIR ? ((c & 1) + 2 * G * (c >> 1)) : G * c;
+}
+template <bool PAIR, int G>
+__host__ __device__ constexpr int owner_of(int k) {
+    return PAIR ? ((k >> 1) % G) : (k % G);
+}
+template <bool PAIR, int G>
+__host__ __device__ constexpr int reg_of(int k) {
+    return PAIR ? (2 * (k / (2 * G)) + (k & 1)) : (k / G);
+}
+
+// Row pitch in elements.  FP32: pitch = GP x odd (GP = max(G, 2)), the smallest such value
+// >= smax.  Then both shared-memory access shapes are conflict free: a half warp's 64-bit
+// row read (32/G rows x G pairs) starts the rows in distinct 4-byte bank groups, and a
+// warp's transposed write or read (G rows k = 2g + b, G apart by 2, x 32/G consecutive
+// rows i) places the G rows 2 x pitch = 8 x odd banks apart (G = 4).  FP64: smax + 1.
 template <typename T>
 __host__ __device__ constexpr int pitch_of(int smax, int g) {
-    return sizeof(T) == 8 ? smax + 1 : g * (((smax + g - 1) / g) | 1);
+    return sizeof(T) == 8 ? smax + 1 : (g < 2 ? 2 : g) * (((smax + (g < 2 ? 2 : g) - 1) / (g < 2 ? 2 : g)) | 1);
 }
 
 // A thread's register-cached row entries (CH columns).  FP32 keeps them as float2 pairs,
@@ -227,9 +246,11 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int i = warp * R + (lane % R);   // row (factor) of this thread
-    const int g = lane / R;                // column group: columns k = g + G*c
-    const bool own_diag = (i % G) == g;    // this thread holds column k = i of its row
-    const int c_diag = i / G;
+    const int g = lane / R;                // column group of this thread within the row
+    constexpr bool PAIR = sizeof(T) == 4;
+    const int k0 = PAIR ? 2 * g : g;       // first column of this thread
+    const bool own_diag = owner_of<PAIR, G>(i) == g;   // this thread holds column k = i of its row
+    const int c_diag = reg_of<PAIR, G>(i);
     const int n = a.tb.n_det;
     const T* __restrict__ Ltab = Num<T>::L(a.tb);
     const int count = *a.count;
@@ -239,9 +260,15 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
     const T ninf = Num<T>::ninf();
     unsigned long long acc_it = 0, acc_msg = 0, acc_def = 0, acc_shots = 0, acc_fc = 0, acc_fcr = 0;
 
-    T* const row_l = Lm + i * P + g;     // element c at [G*c]
-    T* const row_m = Mt + i * P + g;     // incoming messages M[k][i], element c at [G*c]
-    T* const col_m = Mt + g * P + i;     // own outputs M[i][k] live at Mt[k][i], element c at [G*P*c]
+    T* const row_l = Lm + i * P + k0;    // priors l_ik, register c at [col_off(c)]
+    T* const row_m = Mt + i * P + k0;    // incoming messages M[k][i]
+    T* const col_m = Mt + k0 * P + i;    // own outputs M[i][k] live at Mt[k][i], register c at [col_off(c) P]
+#define COL(c) (k0 + col_off<PAIR, G>(c))
+#define RL(c) row_l[col_off<PAIR, G>(c)]
+#define RM(c) row_m[col_off<PAIR, G>(c)]
+#define CM(c) col_m[col_off<PAIR, G>(c) * P]
+#define RL2(j) (*reinterpret_cast<const float2*>(row_l + col_off<PAIR, G>(2 * (j))))
+#define RM2(j) (*reinterpret_cast<const float2*>(row_m + col_off<PAIR, G>(2 * (j))))
 
     for (;;) {
         if (tid == 0) sh_item = atomicAdd(a.next, 1);
@@ -425,11 +452,10 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                         const float2 ainv2 = make_float2(ainv, ainv);
 #pragma unroll
                         for (int j = 0; j < CH / 2; ++j)
-                            q.p[j] = __ffma2_rn(make_float2(row_m[G * 2 * j], row_m[G * (2 * j + 1)]), ainv2,
-                                                make_float2(row_l[G * 2 * j], row_l[G * (2 * j + 1)]));
+                            q.p[j] = __ffma2_rn(RM2(j), ainv2, RL2(j));
                     } else {
 #pragma unroll
-                        for (int c = 0; c < CH; ++c) q[c] = B2<T>::fma_(row_m[G * c], ainv, row_l[G * c]);
+                        for (int c = 0; c < CH; ++c) q[c] = B2<T>::fma_(RM(c), ainv, RL(c));
                     }
                 } else if constexpr (std::is_same<T, float>::value) {
                     // two columns per packed instruction; same roundings as the scalar form
@@ -438,21 +464,21 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
 #pragma unroll
                     for (int j = 0; j < CH / 2; ++j) {
                         const int c = 2 * j;
-                        const float2 l = make_float2(row_l[G * c], row_l[G * (c + 1)]);
-                        const float2 x = make_float2(row_m[G * c], row_m[G * (c + 1)]);
+                        const float2 l = RL2(j);
+                        const float2 x = RM2(j);
                         float2 own;
                         if constexpr (REG)
                             own = mo.p[j];
                         else
-                            own = make_float2(col_m[G * P * c], col_m[G * P * (c + 1)]);
+                            own = make_float2(CM(c), CM(c + 1));
                         q.p[j] = __ffma2_rn(x, ainv2, l);
                         const float2 lam = __fadd2_rn(l, __fadd2_rn(own, x));
                         b0 |= (Mask)(lam.x > 0.f ? 1u : 0u) << c;
                         b1 |= (Mask)(lam.y > 0.f ? 1u : 0u) << (c + 1);
-                        if (tr_on && trl && g + G * c < s)
-                            trl[((size_t)shot * a.s_cap + i) * a.s_cap + g + G * c] = lam.x * (float)kLn2;
-                        if (tr_on && trl && g + G * (c + 1) < s)
-                            trl[((size_t)shot * a.s_cap + i) * a.s_cap + g + G * (c + 1)] = lam.y * (float)kLn2;
+                        if (tr_on && trl && COL(c) < s)
+                            trl[((size_t)shot * a.s_cap + i) * a.s_cap + COL(c)] = lam.x * (float)kLn2;
+                        if (tr_on && trl && COL(c + 1) < s)
+                            trl[((size_t)shot * a.s_cap + i) * a.s_cap + COL(c + 1)] = lam.y * (float)kLn2;
                     }
                     bits = b0 | b1;
                     if (!REG && own_diag) {
@@ -460,8 +486,8 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                         bits = (bits & ~((Mask)1 << c_diag)) | ((Mask)(lam > 0.f ? 1u : 0u) << c_diag);
                         if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + i] = lam * (float)kLn2;
                     }
-                    if (REG && am_prev % G == g) {
-                        const int ca = am_prev / G;
+                    if (REG && owner_of<PAIR, G>(am_prev) == g) {
+                        const int ca = reg_of<PAIR, G>(am_prev);
                         const float lam = Lm[i * P + am_prev] + (out_am + Mt[i * P + am_prev]);
                         bits = (bits & ~((Mask)1 << ca)) | ((Mask)(lam > 0.f ? 1u : 0u) << ca);
                         if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + am_prev] = lam * (float)kLn2;
@@ -470,17 +496,17 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                     Mask b0 = 0, b1 = 0;
 #pragma unroll
                     for (int c = 0; c < CH; ++c) {
-                        const T l = row_l[G * c];
-                        const T x = row_m[G * c];
-                        const T own = REG ? mo[REG ? c : 0] : col_m[G * P * c];
+                        const T l = RL(c);
+                        const T x = RM(c);
+                        const T own = REG ? mo[REG ? c : 0] : CM(c);
                         q[c] = B2<T>::fma_(x, ainv, l);
                         const T lam = l + (own + x);
                         if (c & 1)
                             b1 |= (Mask)(lam > T(0) ? 1u : 0u) << c;
                         else
                             b0 |= (Mask)(lam > T(0) ? 1u : 0u) << c;
-                        if (tr_on && trl && g + G * c < s)
-                            trl[((size_t)shot * a.s_cap + i) * a.s_cap + g + G * c] = lam * (T)kLn2;
+                        if (tr_on && trl && COL(c) < s)
+                            trl[((size_t)shot * a.s_cap + i) * a.s_cap + COL(c)] = lam * (T)kLn2;
                     }
                     bits = b0 | b1;
                     if (!REG && own_diag) {
@@ -489,22 +515,23 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                         bits = (bits & ~((Mask)1 << c_diag)) | ((Mask)(lam > T(0) ? 1u : 0u) << c_diag);
                         if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + i] = lam * (T)kLn2;
                     }
-                    if (REG && am_prev % G == g) {
+                    if (REG && owner_of<PAIR, G>(am_prev) == g) {
                         // the argmax column's own output is out_am, not the generic formula's
-                        const int ca = am_prev / G;
+                        const int ca = reg_of<PAIR, G>(am_prev);
                         const T lam = Lm[i * P + am_prev] + (out_am + Mt[i * P + am_prev]);
                         bits = (bits & ~((Mask)1 << ca)) | ((Mask)(lam > T(0) ? 1u : 0u) << ca);
                         if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + am_prev] = lam * (T)kLn2;
                     }
                 }
             }
-            int cnt = sizeof(Mask) == 8 ? __popcll((unsigned long long)bits) : __popc((unsigned)bits);
-            int chosen = bits ? g + G * ((sizeof(Mask) == 8 ? __ffsll((long long)bits) : __ffs((int)bits)) - 1) : -1;
+            // kept count << 16 plus (first kept column + 1), summed over the row's G threads:
+            // the count is exact, the column is the row's only kept one when the count is 1
+            int pk = ((sizeof(Mask) == 8 ? __popcll((unsigned long long)bits) : __popc((unsigned)bits)) << 16) +
+                     (bits ? COL((sizeof(Mask) == 8 ? __ffsll((long long)bits) : __ffs((int)bits)) - 1) + 1 : 0);
 #pragma unroll
-            for (int off = R; off < 32; off <<= 1) {
-                cnt += __shfl_xor_sync(kFull, cnt, off);
-                chosen = max(chosen, __shfl_xor_sync(kFull, chosen, off));
-            }
+            for (int off = R; off < 32; off <<= 1) pk += __shfl_xor_sync(kFull, pk, off);
+            const int cnt = pk >> 16;
+            const int chosen = (pk & 0xFFFF) - 1;
             const int conv = __syncthreads_and(t > 0 && (!act || cnt == 1));
 
             if (t > 0) {
@@ -527,12 +554,12 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                         if (open) {
 #pragma unroll
                             for (int c = 0; c < CH; ++c) {
-                                const int k = g + G * c;
+                                const int k = COL(c);
                                 if (k == i || !matched[k]) {
-                                    const T own = REG ? mo[REG ? c : 0] : col_m[G * P * c];
-                                    T lam = row_l[G * c] + (own + row_m[G * c]);
+                                    const T own = REG ? mo[REG ? c : 0] : CM(c);
+                                    T lam = RL(c) + (own + RM(c));
                                     if (!REG && k == i) lam = lii;
-                                    if (REG && k == am_prev) lam = row_l[G * c] + (out_am + row_m[G * c]);
+                                    if (REG && k == am_prev) lam = RL(c) + (out_am + RM(c));
                                     if (bk < 0 || lam > bl) {
                                         bl = lam;
                                         bk = k;
@@ -654,7 +681,7 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                     }
                     m1 = a1;
                     m2 = a2;
-                    am = ac < CH ? g + G * ac : 0x7fffffff;
+                    am = ac < CH ? COL(ac) : 0x7fffffff;
                 } else {
                     T a1 = ninf, a2 = ninf, b1 = ninf, b2 = ninf;
                     int ac = 0x7fffffff, bc = 0x7fffffff;
@@ -674,8 +701,8 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                         }
                     }
                     // column indices of the two partial maxima (ties to the smaller column)
-                    int ka = ac < CH ? g + G * ac : 0x7fffffff;
-                    int kb = bc < CH ? g + G * bc : 0x7fffffff;
+                    int ka = ac < CH ? COL(ac) : 0x7fffffff;
+                    int kb = bc < CH ? COL(bc) : 0x7fffffff;
                     combine_max(a1, a2, ka, b1, b2, kb);
                     m1 = a1;
                     m2 = a2;
@@ -729,20 +756,20 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                             const float2 y = __ffma2_rn(ncf, q.p[j], A2);
                             const float2 lg = make_float2(B2<float>::lg2(y.x), B2<float>::lg2(y.y));
                             const float2 out = __ffma2_rn(lg, neg1, nm1);
-                            col_m[G * P * 2 * j] = out.x;
-                            col_m[G * P * (2 * j + 1)] = out.y;
+                            CM(2 * j) = out.x;
+                            CM(2 * j + 1) = out.y;
                             if constexpr (REG) mo.p[j] = out;
                         }
                     } else {
 #pragma unroll
                         for (int c = 0; c < CH; ++c) {
                             const T out = -m1 - B2<T>::lg2(B2<T>::fma_(-cf, q[c], Aa));
-                            col_m[G * P * c] = out;
+                            CM(c) = out;
                             if (REG) mo[REG ? c : 0] = out;
                         }
                     }
                     const T oam = -m2 - B2<T>::lg2(S - T(1));
-                    if (am % G == g) Mt[am * P + i] = oam;
+                    if (owner_of<PAIR, G>(am) == g) Mt[am * P + i] = oam;
                     if (REG) {
                         am_prev = am;
                         out_am = oam;
@@ -787,6 +814,12 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
         atomicAdd(a.ctr + C_FC_RUNS, acc_fc);
         atomicAdd(a.ctr + C_FC_ROUNDS, acc_fcr);
     }
+#undef COL
+#undef RL
+#undef RM
+#undef CM
+#undef RL2
+#undef RM2
 }
 
 // ------------------------------------------------------------------ tier table
