@@ -36,6 +36,11 @@ KERNEL_OF = {"tier1": "decode_smem_kernel<float, CH=32, G=1> (s <= 32)",
              "tier6": "decode_smem_kernel<float, CH=36, G=4> (s <= 144)",
              "tier7": "decode_smem_kernel<float, CH=40, G=4> (s <= 160)",
              "global": "decode_stream_kernel<float> (s > 160)"}
+# DRAM bytes (read + write) per decoded shot of each FP32 tier kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of the 65,536-shot case of this workload,
+# divided by the shots the launch decoded; a full launch's traffic is this times its shots.
+DRAM_BYTES_PER_SHOT = {"tier4": 8.524e6 / 10172, "tier5": 11.992e6 / 26656, "tier6": 11.057e6 / 21645,
+                       "tier7": 7.433e6 / 5503}
 METRIC = "decoded shots/s & msg-updates/s vs HBM roofline (d=13 circuit); p50/p99 latency"
 WORKLOAD = "rotated surface code memory-Z circuit, d=13, 13 rounds, uniform depolarizing p=0.005 " \
            "(gates, idles, data before rounds, reset/measure flips); 10^6 shots per step; BP4M, " \
@@ -55,6 +60,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--shots", type=int, default=SHOTS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    # message storage: fp32 (the configuration's, default) or the 16-bit forms (FP32 math)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
     return ap.parse_args()
 
 
@@ -174,7 +181,7 @@ def run_ours(args, rank, world, local):
         dist.init_process_group("nccl")
     g = pkg.Graph(D, "circuit", P)
     info = g.info()
-    opts = pkg.make_opts(precision="fp32", early_exit=True, decoder="bp4m")
+    opts = pkg.make_opts(precision=args.precision, early_exit=True, decoder="bp4m")
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     shots = args.shots
@@ -272,10 +279,10 @@ def run_ours(args, rank, world, local):
     line = {
         "metric": METRIC, "value": value, "unit": "shots/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (Philox-sampled circuit noise)",
-        "config": {"workload": WORKLOAD, "d": D, "p": P, "rounds": D, "detectors": info["n_det"][0],
+        "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "fp16": "f16 messages, f32 math", "bf16": "bf16 messages, f32 math"}[args.precision], "data": "synthetic (Philox-sampled circuit noise)",
+        "config": {"workload": WORKLOAD.replace("FP32 messages", {"fp32": "FP32 messages", "fp16": "FP16 messages (FP32 arithmetic)", "bf16": "BF16 messages (FP32 arithmetic)"}[args.precision]), "d": D, "p": P, "rounds": D, "detectors": info["n_det"][0],
                    "graph_edges": info["n_edges"][0], "shots_per_step": shots, "iters": T,
-                   "decoder": "BP4M early exit", "precision": "fp32",
+                   "decoder": "BP4M early exit", "precision": args.precision,
                    "l2": "256 MB buffer written between timed steps; per-step syndromes (148 MB) exceed L2",
                    "parallelism": "shots sharded across ranks, no collective on the data path"},
         "msg_updates_per_s": all_msg / (t_max / 1e3),
@@ -285,7 +292,10 @@ def run_ours(args, rank, world, local):
         "ler": totals["fail"] / max(totals["shots"], 1),
         "mean_iters": totals["iters"] / max(totals["shots"], 1),
         "roofline": {"bound": "alu", "kernel": KERNEL_OF.get(dom, dom), "achieved": achieved,
-                     "peak": peak, "unit": "Gmsg/s", "frac": achieved / peak, "traffic": None,
+                     "peak": peak, "unit": "Gmsg/s", "frac": achieved / peak,
+                     "traffic": (DRAM_BYTES_PER_SHOT[dom] * dp["shots"] / max(dp["launches"], 1)
+                                 if dom in DRAM_BYTES_PER_SHOT and args.precision == "fp32" else None),
+                     "traffic_unit": "bytes per launch (ncu DRAM read + write, 65,536-shot capture scaled by shots)",
                      "peak_basis": "MUFU: one ex2 (32/clk/SM) + one lg2 (16/clk/SM) per message update = "
                                    "3/32 SM-cycles; x %d SMs x %.0f MHz (median SM clock in the timed region)"
                                    % (NUM_SMS, sm_mhz),

@@ -68,6 +68,12 @@ typedef struct {
 
 #define BP4M_FP64 0
 #define BP4M_FP32 1
+/* 16-bit message storage with FP32 priors and arithmetic: messages are rounded to nearest
+   (saturating at the largest finite value) when stored and read back exactly.  Shared-
+   memory tiers only; shots with more than 160 unsatisfied detectors use FP32 messages.
+   Not for B-BP4MF or bp4m_decode_noalloc (BP4M_EUNSUPPORTED). */
+#define BP4M_FP16 2
+#define BP4M_BF16 3
 
 #define BP4M_DEC_BP4M   0  /* Sec. "Belief Propagation for Matching (BP4M)" */
 #define BP4M_DEC_BP4MF  1  /* Sec. "BP4M Forced (BP4MF)"; alpha != 1 gives Memory-BP4MF */
@@ -75,7 +81,7 @@ typedef struct {
                               the Tanner graph, then BP4MF on priors reweighted by its posteriors */
 
 typedef struct {
-    int precision;   /* BP4M_FP64 or BP4M_FP32: message storage and arithmetic */
+    int precision;   /* BP4M_FP64, BP4M_FP32 (messages and arithmetic), BP4M_FP16, BP4M_BF16 */
     int early_exit;  /* BP4M only. 1: output the first converged iteration.
                         0: run all iterations, keep the lightest converged candidate */
     int decoder;     /* BP4M_DEC_BP4M, BP4M_DEC_BP4MF or (sample_and_decode, code capacity)

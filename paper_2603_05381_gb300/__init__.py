@@ -12,7 +12,7 @@ import ctypes
 import numpy as np
 
 from . import _capi
-from ._capi import (CIRCUIT, CODE_CAPACITY, DEC_BBP4MF, DEC_BP4M, DEC_BP4MF, FP32, FP64, PRIOR_2P3,
+from ._capi import (CIRCUIT, CODE_CAPACITY, DEC_BBP4MF, DEC_BP4M, DEC_BP4MF, BF16, FP16, FP32, FP64, PRIOR_2P3,
                     PRIOR_P, Bp4mError, check, load)
 
 __all__ = ["Graph", "Bp4mError", "load", "version", "FP32", "FP64", "DEC_BP4M", "DEC_BP4MF"]
@@ -54,7 +54,7 @@ def _stream(stream):
 def make_opts(precision=FP32, early_exit=True, decoder="bp4m", alpha=1.0, type=0):
     dec = ({"bp4m": DEC_BP4M, "bp4mf": DEC_BP4MF, "bbp4mf": DEC_BBP4MF}[decoder] if isinstance(decoder, str)
            else int(decoder))
-    prec = {"fp32": FP32, "fp64": FP64}[precision] if isinstance(precision, str) else int(precision)
+    prec = {"fp32": FP32, "fp64": FP64, "fp16": FP16, "bf16": BF16}[precision] if isinstance(precision, str) else int(precision)
     return _capi.Opts(prec, 1 if early_exit else 0, dec, float(alpha), int(type))
 
 

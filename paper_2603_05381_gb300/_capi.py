@@ -17,6 +17,8 @@ PRIOR_P = 0
 PRIOR_2P3 = 1
 FP64 = 0
 FP32 = 1
+FP16 = 2
+BF16 = 3
 DEC_BP4M = 0
 DEC_BP4MF = 1
 DEC_BBP4MF = 2

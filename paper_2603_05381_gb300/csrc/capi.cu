@@ -106,7 +106,7 @@ struct bp4m_graph {
     int* rw_off[2] = {nullptr, nullptr};
     uint32_t* rw_adj[2] = {nullptr, nullptr};
     int64_t table_bytes = 0;
-    bool prepared[2] = {false, false};
+    bool prepared[4] = {false, false, false, false};
     Workspace ws;
     // measurement: event pairs around every launch while profiling is on
     struct ProfEvent {
@@ -373,8 +373,11 @@ int ensure_qbp_ws(bp4m_graph* g, int64_t cap) {
 
 int check_opts(const bp4m_graph* g, const bp4m_opts* o, int iters) {
     if (!o) return fail(BP4M_EINVAL, "opts is NULL");
-    if (o->precision != BP4M_FP64 && o->precision != BP4M_FP32)
-        return fail(BP4M_EINVAL, "precision must be BP4M_FP64 or BP4M_FP32");
+    if (o->precision != BP4M_FP64 && o->precision != BP4M_FP32 && o->precision != BP4M_FP16 &&
+        o->precision != BP4M_BF16)
+        return fail(BP4M_EINVAL, "precision must be BP4M_FP64, BP4M_FP32, BP4M_FP16 or BP4M_BF16");
+    if (o->decoder == BP4M_DEC_BBP4MF && (o->precision == BP4M_FP16 || o->precision == BP4M_BF16))
+        return fail(BP4M_EUNSUPPORTED, "B-BP4MF runs in FP32 or FP64");
     if (o->decoder != BP4M_DEC_BP4M && o->decoder != BP4M_DEC_BP4MF && o->decoder != BP4M_DEC_BBP4MF)
         return fail(BP4M_EINVAL, "unknown decoder");
     if (o->decoder == BP4M_DEC_BBP4MF && g->host.model != BP4M_CODE_CAPACITY)
@@ -400,10 +403,13 @@ int decode_device(bp4m_graph* g, int ty, const uint32_t* synd, int64_t shots, in
                   const bp4m_opts* o, uint8_t* obs_pred, uint8_t* flags, int16_t* iters,
                   const bp4m_trace* tr, cudaStream_t st, const Stage2* rw = nullptr) {
     Workspace& w = g->ws;
-    const int prec = o->precision == BP4M_FP64 ? 0 : 1;
-    if (!g->prepared[prec]) {
-        CK(prepare_decode_kernels(prec));
-        g->prepared[prec] = true;
+    // pio: storage of the shared-memory tiers (0 FP64, 1 FP32, 2 FP16, 3 BF16); prec: the
+    // arithmetic type of everything else (tables, global tier)
+    const int pio = o->precision == BP4M_FP64 ? 0 : o->precision == BP4M_FP32 ? 1 : o->precision;
+    const int prec = pio == 0 ? 0 : 1;
+    if (!g->prepared[pio]) {
+        CK(prepare_decode_kernels(pio));
+        g->prepared[pio] = true;
     }
     const TierPlan plan = tier_plan(prec);
     CK(cudaMemsetAsync(w.small, 0, (2 * kTiers + 1) * sizeof(int32_t), st));
@@ -479,7 +485,7 @@ int decode_device(bp4m_graph* g, int ty, const uint32_t* synd, int64_t shots, in
         a.next = w.small + kTiers + tier;
         a.tier = tier;
         ProfScope ps(g, tier, st);
-        CK(launch_decode_tier(prec, tier, a, g->num_sms, st));
+        CK(launch_decode_tier(pio, tier, a, g->num_sms, st));
         ps.end();
     }
     CK(cudaEventSynchronize(w.ev_small));
@@ -488,7 +494,7 @@ int decode_device(bp4m_graph* g, int ty, const uint32_t* synd, int64_t shots, in
         const int max_s = w.host_small[2 * kTiers];
         int gsmax = 0;
         const size_t slot_bytes = global_slot_bytes(prec, max_s, &gsmax);
-        int slots = std::min(n_glob, g->num_sms);
+        int slots = std::min(n_glob, g->num_sms * global_blocks_per_sm(prec, max_s));
         const size_t budget = (size_t)16 << 30;
         while (slots > 1 && (size_t)slots * slot_bytes > budget) --slots;
         int rc = ensure_gscratch(g, (size_t)slots * slot_bytes);
@@ -930,6 +936,8 @@ int bp4m_decode_noalloc(const bp4m_graph* g, const uint32_t* syndromes, int64_t 
     if (shots < 0 || shots > 0x7fffffff) return fail(BP4M_EINVAL, "shots out of range");
     int rc = check_opts(g, opts, iters);
     if (rc) return rc;
+    if (opts->precision == BP4M_FP16 || opts->precision == BP4M_BF16)
+        return fail(BP4M_EUNSUPPORTED, "bp4m_decode_noalloc runs in FP32 or FP64");
     int dev = 0;
     CK(cudaGetDevice(&dev));
     if (!g->uploaded || g->device != dev)

@@ -24,6 +24,8 @@
 // the factor k side; Lm[i][k] = l_ik.  Row i is processed by G threads, thread g taking
 // the columns of col_off() (FP32: adjacent pairs 2g, 2g+1, then every 2G; FP64: g + G*c).  The update is in place: every thread caches its row in registers,
 // the block synchronises, then each thread writes its outputs M'[i][k] into Mt[k][i].
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -152,6 +154,66 @@ __host__ __device__ constexpr int pitch_of(int smax, int g) {
     return sizeof(T) == 8 ? smax + 1 : (g < 2 ? 2 : g) * (((smax + (g < 2 ? 2 : g) - 1) / (g < 2 ? 2 : g)) | 1);
 }
 
+// Storage of the message matrix.  MS = T keeps messages in the arithmetic type; MS = __half
+// or __nv_bfloat16 (with T = float) stores them in 16 bits, converted with round to nearest
+// and saturation to the largest finite value on the way in, and exactly to FP32 on the way
+// out; all arithmetic stays FP32.
+template <typename MS, typename T>
+struct MsgIO {
+    static __device__ __forceinline__ T ld(const MS* p) { return *p; }
+    static __device__ __forceinline__ void st(MS* p, T v) { *p = v; }
+    static __device__ __forceinline__ T zero_store() { return T(0); }
+};
+
+template <>
+struct MsgIO<__half, float> {
+    static __device__ __forceinline__ float ld(const __half* p) { return __half2float(*p); }
+    static __device__ __forceinline__ float2 ld2(const __half* p) {
+        return __half22float2(*reinterpret_cast<const __half2*>(p));
+    }
+    // pack (lo, hi) with saturation; returns the packed pair
+    static __device__ __forceinline__ unsigned pack(float lo, float hi) {
+        unsigned r;
+        asm("cvt.rn.satfinite.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+        return r;
+    }
+    static __device__ __forceinline__ float2 unpack(unsigned r) {
+        return __half22float2(*reinterpret_cast<const __half2*>(&r));
+    }
+    static __device__ __forceinline__ void st(__half* p, float v) {
+        const unsigned r = pack(v, 0.f);
+        *reinterpret_cast<unsigned short*>(p) = (unsigned short)(r & 0xFFFFu);
+    }
+};
+
+template <>
+struct MsgIO<__nv_bfloat16, float> {
+    static __device__ __forceinline__ float ld(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ float2 ld2(const __nv_bfloat16* p) {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+    }
+    static __device__ __forceinline__ unsigned pack(float lo, float hi) {
+        unsigned r;
+        asm("cvt.rn.satfinite.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+        return r;
+    }
+    static __device__ __forceinline__ float2 unpack(unsigned r) {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&r));
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16* p, float v) {
+        const unsigned r = pack(v, 0.f);
+        *reinterpret_cast<unsigned short*>(p) = (unsigned short)(r & 0xFFFFu);
+    }
+};
+
+// Pitch of the message matrix in elements.  16-bit storage: 2G x odd, so that the 32-bit
+// pair reads of a warp (32/G rows x G pairs) and its transposed 16-bit writes (G rows,
+// 2 apart, x 32/G consecutive columns) are free of bank conflicts.
+template <typename T, typename MS>
+__host__ __device__ constexpr int msg_pitch_of(int smax, int g) {
+    return sizeof(MS) == 2 ? 2 * g * (((smax + 2 * g - 1) / (2 * g)) | 1) : pitch_of<T>(smax, g);
+}
+
 // A thread's register-cached row entries (CH columns).  FP32 keeps them as float2 pairs,
 // columns (2j, 2j+1) in one 64-bit register pair, so that the packed FP32x2 add and FMA of
 // sm_100 and later apply to two columns per instruction.
@@ -214,17 +276,21 @@ __host__ __device__ constexpr int blocks_for(int nt, int elem_bytes) {
 // RW = true: the B-BP4MF second stage.  The shot's priors, pair weights and parities are
 // computed in the block by Dijkstra from every defect over per-qubit weights derived from
 // the first stage's posteriors (instead of being gathered from the static tables).
-template <typename T, int CH, int G, bool TRACE, bool REG, bool RW = false>
+template <typename T, int CH, int G, bool TRACE, bool REG, bool RW = false, typename MS = T>
 __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof(T))) decode_smem_kernel(const DecodeArgs a) {
     constexpr int SMAX = CH * G;
     constexpr int NT = SMAX * G;
     constexpr int R = 32 / G;
-    constexpr int P = pitch_of<T>(SMAX, G);
+    constexpr int P = pitch_of<T>(SMAX, G);          // priors
+    constexpr int PM = msg_pitch_of<T, MS>(SMAX, G);  // messages
+    constexpr bool HALF = sizeof(MS) == 2;
+    static_assert(!HALF || sizeof(T) == 4, "16-bit messages use FP32 arithmetic");
+    using IO = MsgIO<MS, T>;
     static_assert(NT % 32 == 0 && NT <= 1024, "block size");
     using Mask = typename std::conditional<(CH > 32), unsigned long long, unsigned int>::type;
     extern __shared__ __align__(16) unsigned char smem[];
-    T* Mt = reinterpret_cast<T*>(smem);          // Mt[i][k] = M[k][i]; diagonal kept 0
-    T* Lm = Mt + SMAX * P;                          // Lm[i][k] = l_ik in log2 units, -inf past s
+    MS* Mt = reinterpret_cast<MS*>(smem);        // Mt[i][k] = M[k][i]; diagonal kept 0
+    T* Lm = reinterpret_cast<T*>(smem + ((size_t)SMAX * PM * sizeof(MS) + 15) / 16 * 16);  // Lm[i][k] = l_ik (log2), -inf past s
     T* Dg = Lm + SMAX * P;                          // Dg[i] = M[i][i] (factor i to its boundary variable)
     double* rowacc = reinterpret_cast<double*>(Dg + SMAX + (SMAX & 1));
     int* dets = reinterpret_cast<int*>(rowacc + SMAX);
@@ -261,14 +327,21 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
     unsigned long long acc_it = 0, acc_msg = 0, acc_def = 0, acc_shots = 0, acc_fc = 0, acc_fcr = 0;
 
     T* const row_l = Lm + i * P + k0;    // priors l_ik, register c at [col_off(c)]
-    T* const row_m = Mt + i * P + k0;    // incoming messages M[k][i]
-    T* const col_m = Mt + k0 * P + i;    // own outputs M[i][k] live at Mt[k][i], register c at [col_off(c) P]
+    MS* const row_m = Mt + i * PM + k0;  // incoming messages M[k][i]
+    MS* const col_m = Mt + k0 * PM + i;  // own outputs M[i][k] live at Mt[k][i], register c at [col_off(c) PM]
 #define COL(c) (k0 + col_off<PAIR, G>(c))
 #define RL(c) row_l[col_off<PAIR, G>(c)]
-#define RM(c) row_m[col_off<PAIR, G>(c)]
-#define CM(c) col_m[col_off<PAIR, G>(c) * P]
+#define RM(c) IO::ld(row_m + col_off<PAIR, G>(c))
+#define CMP(c) (col_m + col_off<PAIR, G>(c) * PM)
+#define CM(c) IO::ld(CMP(c))
 #define RL2(j) (*reinterpret_cast<const float2*>(row_l + col_off<PAIR, G>(2 * (j))))
-#define RM2(j) (*reinterpret_cast<const float2*>(row_m + col_off<PAIR, G>(2 * (j))))
+#define RM2(j) m_ld2(row_m + col_off<PAIR, G>(2 * (j)))
+    auto m_ld2 = [](const MS* p) -> float2 {
+        if constexpr (HALF)
+            return IO::ld2(p);
+        else
+            return *reinterpret_cast<const float2*>(p);
+    };
 
     for (;;) {
         if (tid == 0) sh_item = atomicAdd(a.next, 1);
@@ -316,7 +389,7 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                 const T* trow = Ltab + (size_t)dets[r] * n;
                 for (int k = lane; k < SMAX; k += 32) {
                     Lm[r * P + k] = k < s ? (T)(__ldg(trow + dets[k]) * (T)kLog2e) : ninf;
-                    Mt[r * P + k] = T(0);
+                    Mt[r * PM + k] = MS(0.f);
                 }
             }
         } else {
@@ -394,7 +467,7 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                     } else {
                         Lm[r * P + k] = ninf;
                     }
-                    Mt[r * P + k] = T(0);
+                    Mt[r * PM + k] = MS(0.f);
                 }
             }
         }
@@ -488,7 +561,7 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                     }
                     if (REG && owner_of<PAIR, G>(am_prev) == g) {
                         const int ca = reg_of<PAIR, G>(am_prev);
-                        const float lam = Lm[i * P + am_prev] + (out_am + Mt[i * P + am_prev]);
+                        const float lam = Lm[i * P + am_prev] + (out_am + IO::ld(Mt + i * PM + am_prev));
                         bits = (bits & ~((Mask)1 << ca)) | ((Mask)(lam > 0.f ? 1u : 0u) << ca);
                         if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + am_prev] = lam * (float)kLn2;
                     }
@@ -518,7 +591,7 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                     if (REG && owner_of<PAIR, G>(am_prev) == g) {
                         // the argmax column's own output is out_am, not the generic formula's
                         const int ca = reg_of<PAIR, G>(am_prev);
-                        const T lam = Lm[i * P + am_prev] + (out_am + Mt[i * P + am_prev]);
+                        const T lam = Lm[i * P + am_prev] + (out_am + IO::ld(Mt + i * PM + am_prev));
                         bits = (bits & ~((Mask)1 << ca)) | ((Mask)(lam > T(0) ? 1u : 0u) << ca);
                         if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + am_prev] = lam * (T)kLn2;
                     }
@@ -756,27 +829,37 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                             const float2 y = __ffma2_rn(ncf, q.p[j], A2);
                             const float2 lg = make_float2(B2<float>::lg2(y.x), B2<float>::lg2(y.y));
                             const float2 out = __ffma2_rn(lg, neg1, nm1);
-                            CM(2 * j) = out.x;
-                            CM(2 * j + 1) = out.y;
-                            if constexpr (REG) mo.p[j] = out;
+                            if constexpr (HALF) {
+                                // store the rounded pair; the register copy is the stored value,
+                                // so that both ends of a variable see the same message
+                                const unsigned pk2 = IO::pack(out.x, out.y);
+                                *reinterpret_cast<unsigned short*>(CMP(2 * j)) = (unsigned short)(pk2 & 0xFFFFu);
+                                *reinterpret_cast<unsigned short*>(CMP(2 * j + 1)) = (unsigned short)(pk2 >> 16);
+                                if constexpr (REG) mo.p[j] = IO::unpack(pk2);
+                            } else {
+                                *CMP(2 * j) = out.x;
+                                *CMP(2 * j + 1) = out.y;
+                                if constexpr (REG) mo.p[j] = out;
+                            }
                         }
                     } else {
 #pragma unroll
                         for (int c = 0; c < CH; ++c) {
                             const T out = -m1 - B2<T>::lg2(B2<T>::fma_(-cf, q[c], Aa));
-                            CM(c) = out;
+                            *CMP(c) = out;
                             if (REG) mo[REG ? c : 0] = out;
                         }
                     }
-                    const T oam = -m2 - B2<T>::lg2(S - T(1));
-                    if (owner_of<PAIR, G>(am) == g) Mt[am * P + i] = oam;
+                    T oam = -m2 - B2<T>::lg2(S - T(1));
+                    if constexpr (HALF) oam = IO::unpack(IO::pack(oam, 0.f)).x;
+                    if (owner_of<PAIR, G>(am) == g) IO::st(Mt + am * PM + i, oam);
                     if (REG) {
                         am_prev = am;
                         out_am = oam;
                     }
                     if (own_diag) {
-                        if (!REG) Dg[i] = Mt[i * P + i];
-                        Mt[i * P + i] = T(0);
+                        if (!REG) Dg[i] = IO::ld(Mt + i * PM + i);
+                        Mt[i * PM + i] = MS(0.f);
                     }
                 }
             }
@@ -818,6 +901,7 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
 #undef RL
 #undef RM
 #undef CM
+#undef CMP
 #undef RL2
 #undef RM2
 }
@@ -848,12 +932,39 @@ inline int64_t rw_slot_layout(int smax, int nt, int nodes) {
     return (b + 255) / 256 * 256;
 }
 
-template <typename T, int CH, int G>
+template <typename T, int CH, int G, typename MS = T>
 size_t smem_bytes_of() {
     constexpr int SMAX = CH * G;
     constexpr int P = pitch_of<T>(SMAX, G);
-    return (size_t)(2 * SMAX * P + SMAX + (SMAX & 1)) * sizeof(T) +
+    constexpr int PM = msg_pitch_of<T, MS>(SMAX, G);
+    return ((size_t)SMAX * PM * sizeof(MS) + 15) / 16 * 16 + (size_t)(SMAX * P + SMAX + (SMAX & 1)) * sizeof(T) +
            (size_t)SMAX * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 16;
+}
+
+template <typename T, int CH, int G, bool TRACE, bool REG, typename MS = T>
+cudaError_t run_tier(const DecodeArgs& a, int num_sms, cudaStream_t st, bool prepare_only) {
+    const size_t smem = smem_bytes_of<T, CH, G, MS>();
+    auto kern = decode_smem_kernel<T, CH, G, TRACE, REG, false, MS>;
+    if (prepare_only)
+        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CH * G * G, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    kern<<<per_sm * num_sms, CH * G * G, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// Every tier has a production instantiation and a traced one (tests).
+template <typename T, int CH, int G, bool REG, typename MS = T>
+cudaError_t run_tier2(const DecodeArgs& a, int num_sms, cudaStream_t st, bool prep) {
+    const bool tr = a.tr_lambda != nullptr || a.tr_partner != nullptr;
+    if (prep) {
+        cudaError_t e = run_tier<T, CH, G, false, REG, MS>(a, num_sms, st, true);
+        return e != cudaSuccess ? e : run_tier<T, CH, G, true, REG, MS>(a, num_sms, st, true);
+    }
+    return tr ? run_tier<T, CH, G, true, REG, MS>(a, num_sms, st, false)
+              : run_tier<T, CH, G, false, REG, MS>(a, num_sms, st, false);
 }
 
 }  // namespace

@@ -143,6 +143,9 @@ cudaError_t launch_classify(const uint32_t* synd, int64_t shots, int n_words,
                             int16_t* iters, int32_t* tr_defects, const uint8_t* skip,
                             const uint8_t* skip_obs, const int16_t* skip_iters, cudaStream_t st);
 
+// 16-bit message storage (precision 2 = IEEE half, 3 = bfloat16) of the shared-memory tiers.
+cudaError_t launch_decode_tier_half(int precision, int tier, const DecodeArgs& a, int num_sms, cudaStream_t st,
+                                    bool prepare_only);
 // Launch the decoding kernel of shared-memory tier `tier` (1..7) for precision
 // (0 = FP64, 1 = FP32).  Returns cudaSuccess if the tier is empty by construction.
 cudaError_t launch_decode_tier(int precision, int tier, const DecodeArgs& a, int num_sms,
@@ -163,6 +166,8 @@ constexpr double kRwMinWeight = 9.5367431640625e-07;  // 2^-20
 // Global-memory tier.  `slots` CTAs each own one scratch slot of global_slot_bytes() for
 // the batch's largest defect count; a.gsmax must be the value that function reports.
 size_t global_slot_bytes(int precision, int max_s, int* gsmax_out);
+// Resident blocks per SM of the global-memory tier for the batch's largest defect count.
+int global_blocks_per_sm(int precision, int max_s);
 cudaError_t launch_decode_global(int precision, const DecodeArgs& a, int slots,
                                  cudaStream_t st);
 // Shared-memory tier plan for a precision.

@@ -317,6 +317,10 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
 // the update pass.
 constexpr int kStreamWarps = 16;
 constexpr int kStreamThreads = kStreamWarps * 32;
+// Blocks per SM: the 256-column variant (shots of up to 256 defects) runs two, so that one
+// block's L2 latency overlaps the other's arithmetic.
+template <typename T, int CH>
+constexpr int kStreamBlocks = (sizeof(T) == 4 && CH <= 8) ? 2 : 1;
 
 template <typename T>
 __device__ __forceinline__ T warp_max(T v) {
@@ -333,7 +337,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 template <typename T, int CH, bool TRACE>
-__global__ void __launch_bounds__(kStreamThreads, 1) decode_stream_kernel(const DecodeArgs a) {
+__global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_stream_kernel(const DecodeArgs a) {
     constexpr int LD = 32 * CH;
     constexpr int SP = LD + 1;  // stage pitch: odd, so the transposed read is conflict-free
     extern __shared__ __align__(16) unsigned char smem[];
@@ -658,32 +662,6 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 constexpr int kMaxDevices = 64;
 std::atomic<void*> g_noalloc_addr[kMaxDevices];
 
-template <typename T, int CH, int G, bool TRACE, bool REG>
-cudaError_t run_tier(const DecodeArgs& a, int num_sms, cudaStream_t st, bool prepare_only) {
-    const size_t smem = smem_bytes_of<T, CH, G>();
-    auto kern = decode_smem_kernel<T, CH, G, TRACE, REG>;
-    if (prepare_only)
-        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, CH * G * G, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    kern<<<per_sm * num_sms, CH * G * G, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-// Every tier has a production instantiation and a traced one (tests).
-template <typename T, int CH, int G, bool REG>
-cudaError_t run_tier2(const DecodeArgs& a, int num_sms, cudaStream_t st, bool prep) {
-    const bool tr = a.tr_lambda != nullptr || a.tr_partner != nullptr;
-    if (prep) {
-        cudaError_t e = run_tier<T, CH, G, false, REG>(a, num_sms, st, true);
-        return e != cudaSuccess ? e : run_tier<T, CH, G, true, REG>(a, num_sms, st, true);
-    }
-    return tr ? run_tier<T, CH, G, true, REG>(a, num_sms, st, false)
-              : run_tier<T, CH, G, false, REG>(a, num_sms, st, false);
-}
-
 template <typename T>
 cudaError_t dispatch_tier(int tier, const DecodeArgs& a, int num_sms, cudaStream_t st, bool prep);
 
@@ -725,8 +703,9 @@ TierPlan tier_plan(int precision) {
 cudaError_t prepare_decode_kernels(int precision) {
     DecodeArgs dummy;
     for (int tier = 1; tier < kGlobalTier; ++tier) {
-        cudaError_t e = precision == 0 ? dispatch_tier<double>(tier, dummy, 0, 0, true)
-                                       : dispatch_tier<float>(tier, dummy, 0, 0, true);
+        cudaError_t e = precision == 0   ? dispatch_tier<double>(tier, dummy, 0, 0, true)
+                        : precision == 1 ? dispatch_tier<float>(tier, dummy, 0, 0, true)
+                                         : launch_decode_tier_half(precision, tier, dummy, 0, 0, true);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -734,6 +713,7 @@ cudaError_t prepare_decode_kernels(int precision) {
 
 cudaError_t launch_decode_tier(int precision, int tier, const DecodeArgs& a, int num_sms,
                                cudaStream_t st) {
+    if (precision >= 2) return launch_decode_tier_half(precision, tier, a, num_sms, st, false);
     return precision == 0 ? dispatch_tier<double>(tier, a, num_sms, st, false)
                           : dispatch_tier<float>(tier, a, num_sms, st, false);
 }
@@ -811,6 +791,10 @@ int stream_ch(int precision, int max_s) {
 }
 
 }  // namespace
+
+int global_blocks_per_sm(int precision, int max_s) {
+    return (precision != 0 && stream_ch(precision, max_s) == 8) ? kStreamBlocks<float, 8> : 1;
+}
 
 size_t global_slot_bytes(int precision, int max_s, int* gsmax_out) {
     const size_t esz = precision == 0 ? sizeof(double) : sizeof(float);

@@ -1,0 +1,37 @@
+// Decoding with 16-bit message storage (IEEE half or bfloat16): the shared-memory kernel
+// with MS = __half / __nv_bfloat16 and FP32 priors and arithmetic.  Same tiers as FP32;
+// shots past the shared-memory tiers use the FP32 global-memory tier.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "decode_smem.cuh"
+#include "device.cuh"
+
+namespace bp4m {
+namespace {
+
+template <typename MS>
+cudaError_t dispatch_half(int tier, const DecodeArgs& a, int num_sms, cudaStream_t st, bool prep) {
+    switch (tier) {
+        case 1: return run_tier2<float, 32, 1, kReg32[1], MS>(a, num_sms, st, prep);
+        case 2: return run_tier2<float, 32, 2, kReg32[2], MS>(a, num_sms, st, prep);
+        case 3: return run_tier2<float, 24, 4, kReg32[3], MS>(a, num_sms, st, prep);
+        case 4: return run_tier2<float, 28, 4, kReg32[4], MS>(a, num_sms, st, prep);
+        case 5: return run_tier2<float, 32, 4, kReg32[5], MS>(a, num_sms, st, prep);
+        case 6: return run_tier2<float, 36, 4, kReg32[6], MS>(a, num_sms, st, prep);
+        case 7: return run_tier2<float, 40, 4, kReg32[7], MS>(a, num_sms, st, prep);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_decode_tier_half(int precision, int tier, const DecodeArgs& a, int num_sms, cudaStream_t st,
+                                    bool prepare_only) {
+    if (precision == 2) return dispatch_half<__half>(tier, a, num_sms, st, prepare_only);
+    if (precision == 3) return dispatch_half<__nv_bfloat16>(tier, a, num_sms, st, prepare_only);
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace bp4m
