@@ -62,6 +62,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     # message storage: fp32 (the configuration's, default) or the 16-bit forms (FP32 math)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    # decoding-service measurement: circuit graphs of these distances (p = 0.005), requests
+    # of 1..4096 shots arriving as a Poisson process at a fraction of the measured capacity
+    ap.add_argument("--serve-d", default="5,9,13")
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-load", type=float, default=0.5)
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--no-serve", action="store_true")
     return ap.parse_args()
 
 
@@ -146,7 +153,7 @@ def cpu_baseline(n_shots=None, seed=SEED, first_shot=0):
     from oracle.graph import all_pairs, edge_weights_circuit, prior_llr
     from oracle.sampler import graph_sample
     cores = os.cpu_count() or 1
-    n = n_shots or max(16, min(4 * cores, 160))
+    n = n_shots or max(16, min(10 * cores, 400))
     og, _, _ = circuit_graph(D, Noise(P))
     synd, _ = graph_sample(og, np.arange(first_shot, first_shot + n, dtype=np.uint64), seed=seed)
     dets = [np.flatnonzero(r) for r in synd]
@@ -168,6 +175,79 @@ def cpu_baseline(n_shots=None, seed=SEED, first_shot=0):
 
 
 # ---------------------------------------------------------------- our arm
+
+def run_serving(args, dev):
+    """p50/p99 request latency and sustained shots/s of the decoding service (Server) on a
+    Poisson stream of requests of mixed distance: each request a uniform 1..4096-shot slice
+    of pre-sampled syndromes of one of the graphs.  Capacity is measured first by a closed
+    burst of requests; arrivals then run at serve_load x capacity."""
+    import numpy as np
+    import torch
+    import paper_2603_05381_gb300 as pkg
+
+    ds = [int(x) for x in args.serve_d.split(",") if x]
+    rng = np.random.default_rng(SEED)
+    opts = pkg.make_opts(precision=args.precision, early_exit=True)
+    graphs, pools = [], []
+    for d in ds:
+        g = pkg.Graph(d, "circuit", P)
+        nw = g.info()["n_words"][0]
+        pool = 8192
+        synd = torch.empty((pool * nw,), dtype=torch.int32, device=dev)
+        obs = torch.empty((1, pool), dtype=torch.uint8, device=dev)
+        g.sample(synd, obs, first_shot=10**9, seed=SEED)
+        torch.cuda.synchronize()
+        graphs.append(g)
+        pools.append(synd.view(pool, nw).cpu().numpy().view(np.uint32).copy())
+    srv = pkg.Server(slots=args.serve_slots, max_batch_shots=4096)
+    gids = [srv.add_graph(g) for g in graphs]
+
+    def make_request():
+        k = int(rng.integers(0, len(graphs)))
+        n = int(rng.integers(1, 4097))
+        a = int(rng.integers(0, 8192 - n + 1))
+        return k, np.ascontiguousarray(pools[k][a:a + n]), np.empty(n, dtype=np.uint8)
+
+    # warm-up: every graph once in every slot
+    warm = [make_request() for _ in range(4 * len(graphs) * args.serve_slots)]
+    for r in [srv.submit(gids[k], s, T, opts, o) for k, s, o in warm]:
+        srv.wait(r)
+    # capacity: a closed burst
+    burst = [make_request() for _ in range(64)]
+    t0 = time.perf_counter()
+    ids = [srv.submit(gids[k], s, T, opts, o) for k, s, o in burst]
+    for r in ids:
+        srv.wait(r)
+    cap_shots = sum(o.shape[0] for _, _, o in burst) / (time.perf_counter() - t0)
+    mean_req = 2048.5
+    rate = args.serve_load * cap_shots / mean_req
+    reqs = [make_request() for _ in range(args.serve_requests)]
+    gaps = rng.exponential(1.0 / rate, size=len(reqs))
+    st0 = srv.stats()
+    t0 = time.perf_counter()
+    t_next = t0
+    ids = []
+    for (k, s, o), gap in zip(reqs, gaps):
+        t_next += gap
+        while time.perf_counter() < t_next:
+            pass
+        ids.append(srv.submit(gids[k], s, T, opts, o))
+    infos = [srv.wait(r) for r in ids]
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    for g in graphs:
+        g.close()
+    lat = np.array([i["latency_s"] for i in infos]) * 1e3
+    shots = sum(o.shape[0] for _, _, o in reqs)
+    return {"graphs": "rotated memory-Z circuit, d in {%s}, p=%g" % (",".join(map(str, ds)), P),
+            "requests": len(reqs), "request_shots": "uniform 1..4096", "iters": T, "slots": args.serve_slots,
+            "capacity_shots_per_s": cap_shots, "offered_load": args.serve_load,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "sustained_shots_per_s": shots / wall,
+            "batches": st["batches"] - st0["batches"], "merged_requests": st["merged_requests"] - st0["merged_requests"],
+            "max_inflight_batches": st["max_inflight_batches"]}
+
 
 def run_ours(args, rank, world, local):
     import numpy as np
@@ -313,6 +393,8 @@ def run_ours(args, rank, world, local):
                                                              "host outputs (obs, converged, iters) out"},
         "gpu_launches": launches,
     }
+    if rank == 0 and not args.no_serve:
+        line["serving"] = run_serving(args, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if world > 1:

@@ -247,6 +247,62 @@ int bp4m_profile_read(bp4m_graph* g, bp4m_profile_t* out);
 
 void bp4m_free_graph(bp4m_graph* g);
 
+/* ---- Decoding service (no counterpart in the paper: serving infrastructure around the
+   BP4M decode of Sec. "Belief Propagation").
+
+   A request loop over device-resident graphs.  bp4m_server_create starts n_slots worker
+   threads, each with its own non-blocking CUDA stream on the current device.  A worker
+   takes the oldest pending request and merges into it every pending request of the same
+   graph, iterations and options while the merged batch stays within max_batch_shots
+   (continuous batching); its host-to-device copy, decode kernels and device-to-host copy
+   run on its stream, so the slots' batches overlap on the GPU.  Message state and tables
+   stay resident: each slot keeps one workspace per graph it has decoded.  When the device
+   bytes of all workspaces' per-shot buffers would exceed device_budget_bytes (0: no limit),
+   a slot frees its least recently used workspaces before allocating; a batch that still
+   does not fit fails with BP4M_ENOMEM.  (Scratch of the global-memory tier, for shots
+   with more than 160 unsatisfied detectors, grows on demand outside the budget.)  A graph's per-iteration results are
+   bit-identical to bp4m_decode_batch on the same syndromes, alone or merged with others.
+   bp4m_profile_* does not see the service's launches.  Decoders BP4M and BP4MF (any
+   precision); B-BP4MF is BP4M_EUNSUPPORTED. */
+typedef struct bp4m_server bp4m_server;
+
+typedef struct {
+    double t_submit, t_start, t_done;  /* steady-clock seconds */
+    double latency_s;                  /* t_done - t_submit */
+    int64_t batch_shots;               /* shots of the merged batch the request ran in */
+    int slot;                          /* worker slot that ran it */
+} bp4m_request_info;
+
+typedef struct {
+    int64_t batches;               /* batches run */
+    int64_t merged_requests;       /* requests that joined another request's batch */
+    int64_t shots;                 /* shots decoded */
+    int64_t evictions;             /* workspaces freed to stay within the budget */
+    int64_t max_inflight_batches;  /* most batches running at the same time */
+    int64_t pending;               /* requests waiting now */
+    int64_t device_bytes;          /* device bytes of the workspaces now */
+} bp4m_server_stats_t;
+
+/* n_slots in [1, 64]; max_batch_shots in [1, 2^20].  NULL on error (bp4m_last_error). */
+bp4m_server* bp4m_server_create(int n_slots, int64_t max_batch_shots, int64_t device_budget_bytes);
+/* Registers a graph (uploading its tables); returns its id >= 0 or a negative error code.
+   The graph must outlive the server. */
+int bp4m_server_add_graph(bp4m_server* s, bp4m_graph* g);
+/* Queues `shots` syndromes (host, uint32 [shots][n_words] of opts->type, copied before
+   returning) for decoding with `iters` iterations.  obs_pred and converged (uint8 [shots],
+   host; converged may be NULL) are written before the request completes and must stay
+   valid until bp4m_server_wait returns for it.  Returns the request id >= 0 or a negative
+   error code. */
+int64_t bp4m_server_submit(bp4m_server* s, int graph_id, const uint32_t* syndromes, int64_t shots, int iters,
+                           const bp4m_opts* opts, uint8_t* obs_pred, uint8_t* converged);
+/* Waits up to timeout_s seconds (< 0: no limit) for a request; BP4M_OK when it finished
+   (info filled, the request is then forgotten), BP4M_ETIMEOUT if not yet, or the error the
+   request's batch met. */
+int bp4m_server_wait(bp4m_server* s, int64_t request, double timeout_s, bp4m_request_info* info);
+int bp4m_server_stats(bp4m_server* s, bp4m_server_stats_t* out);
+/* Finishes the queued requests, stops the workers and frees the service's device memory. */
+int bp4m_server_destroy(bp4m_server* s);
+
 const char* bp4m_last_error(void);
 
 /* Library version string. */

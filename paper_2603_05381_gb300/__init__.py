@@ -162,3 +162,62 @@ class Graph:
                 "iterations": c.iterations, "msg_updates": c.msg_updates, "defects": c.defects,
                 "forced_runs": c.forced_runs, "forced_rounds": c.forced_rounds,
                 "unconverged_any": c.unconverged_any, "conv_fail_any": c.conv_fail_any}
+
+
+class Server:
+    """Decoding service (bp4m_server_*): worker slots with their own streams decode queued
+    requests of any registered graph, merging compatible pending requests into one batch.
+    Host numpy buffers only."""
+
+    def __init__(self, slots=4, max_batch_shots=4096, device_budget_bytes=0):
+        lib = load()
+        h = lib.bp4m_server_create(int(slots), int(max_batch_shots), int(device_budget_bytes))
+        if not h:
+            raise Bp4mError(-1, lib.bp4m_last_error().decode(errors="replace"))
+        self._h = ctypes.c_void_p(h)
+        self._keep = {}
+
+    def add_graph(self, graph):
+        gid = load().bp4m_server_add_graph(self._h, graph._h)
+        if gid < 0:
+            check(gid)
+        return gid
+
+    def submit(self, graph_id, syndromes, iters, opts, obs_pred, converged=None):
+        """syndromes: uint32 [shots, n_words] (numpy); obs_pred / converged: uint8 [shots]
+        numpy arrays filled when the request completes.  Returns the request id."""
+        shots = obs_pred.shape[0]
+        rid = load().bp4m_server_submit(self._h, int(graph_id), _ptr(syndromes), int(shots), int(iters),
+                                        ctypes.byref(opts), _ptr(obs_pred), _ptr(converged))
+        if rid < 0:
+            check(int(rid))
+        self._keep[rid] = (obs_pred, converged)
+        return rid
+
+    def wait(self, request, timeout=-1.0):
+        """Blocks until the request finished; returns its timing dict."""
+        info = _capi.RequestInfo()
+        rc = load().bp4m_server_wait(self._h, int(request), float(timeout), ctypes.byref(info))
+        if rc != _capi.BP4M_ETIMEOUT:
+            self._keep.pop(request, None)  # finished (or failed): the service forgot it
+        check(rc)
+        return {"t_submit": info.t_submit, "t_start": info.t_start, "t_done": info.t_done,
+                "latency_s": info.latency_s, "batch_shots": info.batch_shots, "slot": info.slot}
+
+    def stats(self):
+        st = _capi.ServerStats()
+        check(load().bp4m_server_stats(self._h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in _capi.ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().bp4m_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -6,6 +6,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbp4m.so")
 
 BP4M_OK = 0
+BP4M_ETIMEOUT = -4
 ERRORS = {-1: "EINVAL", -2: "ENOMEM", -3: "EUNSUPPORTED", -4: "ETIMEOUT", -5: "ECUDA"}
 
 ROTATED = 0
@@ -75,6 +76,17 @@ class Trace(ctypes.Structure):
                 ("flags", ctypes.c_void_p), ("s_cap", ctypes.c_int)]
 
 
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("latency_s", ctypes.c_double), ("batch_shots", ctypes.c_int64), ("slot", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_int64), ("merged_requests", ctypes.c_int64), ("shots", ctypes.c_int64),
+                ("evictions", ctypes.c_int64), ("max_inflight_batches", ctypes.c_int64),
+                ("pending", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
 _P = ctypes.c_void_p
 SIGNATURES = {
     "bp4m_build_graph": (ctypes.c_int, [ctypes.POINTER(Code), ctypes.POINTER(Noise), ctypes.POINTER(_P)]),
@@ -95,6 +107,13 @@ SIGNATURES = {
     "bp4m_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "bp4m_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "bp4m_free_graph": (None, [_P]),
+    "bp4m_server_create": (_P, [ctypes.c_int, ctypes.c_int64, ctypes.c_int64]),
+    "bp4m_server_add_graph": (ctypes.c_int, [_P, _P]),
+    "bp4m_server_submit": (ctypes.c_int64, [_P, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int,
+                                            ctypes.POINTER(Opts), _P, _P]),
+    "bp4m_server_wait": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(RequestInfo)]),
+    "bp4m_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
+    "bp4m_server_destroy": (ctypes.c_int, [_P]),
     "bp4m_last_error": (ctypes.c_char_p, []),
     "bp4m_version": (ctypes.c_char_p, []),
 }

@@ -3,7 +3,15 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -20,6 +28,9 @@ using namespace bp4m;
 namespace {
 
 thread_local std::string g_last_error;
+// set on the decoding service's worker threads: their launches are not profiled (the
+// profile of a graph is single-threaded state)
+thread_local bool tl_no_prof = false;
 
 int fail(int code, const std::string& msg) {
     g_last_error = msg;
@@ -132,7 +143,7 @@ struct ProfScope {
     cudaStream_t st;
     cudaEvent_t a = nullptr;
     ProfScope(bp4m_graph* g_, int slot_, cudaStream_t st_) : g(g_), slot(slot_), st(st_) {
-        if (g->prof_on && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, st);
+        if (g->prof_on && !tl_no_prof && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, st);
     }
     void end() {
         if (!a) return;
@@ -157,7 +168,7 @@ void prof_clear(bp4m_graph* g) {
 }
 
 void prof_add_counters(bp4m_graph* g, const unsigned long long* c) {
-    if (!g->prof_on) return;
+    if (!g->prof_on || tl_no_prof) return;
     for (int t = 0; t < kTiers; ++t) {
         g->prof.msg_updates[t] += c[C_TIER_MSGS + t];
         g->prof.shots[t] += c[C_TIER_SHOTS + t];
@@ -312,8 +323,7 @@ void free_ws(Workspace& w) {
     w = Workspace();
 }
 
-int ensure_ws(bp4m_graph* g, int64_t cap) {
-    Workspace& w = g->ws;
+int ensure_ws(bp4m_graph* g, Workspace& w, int64_t cap) {
     if (w.cap >= cap && w.small) return BP4M_OK;
     const int nt = g->host.n_types;
     void* gs = w.gscratch;
@@ -340,8 +350,9 @@ int ensure_ws(bp4m_graph* g, int64_t cap) {
     return BP4M_OK;
 }
 
-int ensure_gscratch(bp4m_graph* g, size_t bytes) {
-    Workspace& w = g->ws;
+int ensure_ws(bp4m_graph* g, int64_t cap) { return ensure_ws(g, g->ws, cap); }
+
+int ensure_gscratch(Workspace& w, size_t bytes) {
     if (w.gscratch_bytes >= bytes) return BP4M_OK;
     cudaFree(w.gscratch);
     w.gscratch = nullptr;
@@ -351,8 +362,7 @@ int ensure_gscratch(bp4m_graph* g, size_t bytes) {
     return BP4M_OK;
 }
 
-int ensure_qbp_ws(bp4m_graph* g, int64_t cap) {
-    Workspace& w = g->ws;
+int ensure_qbp_ws(bp4m_graph* g, Workspace& w, int64_t cap) {
     if (w.qcap >= cap) return BP4M_OK;
     cudaFree(w.qconv);
     cudaFree(w.qobs);
@@ -399,10 +409,9 @@ struct Stage2 {
     const double* post = nullptr;       // [shots][n_units] posteriors of this type
 };
 
-int decode_device(bp4m_graph* g, int ty, const uint32_t* synd, int64_t shots, int T,
+int decode_device(bp4m_graph* g, Workspace& w, int ty, const uint32_t* synd, int64_t shots, int T,
                   const bp4m_opts* o, uint8_t* obs_pred, uint8_t* flags, int16_t* iters,
                   const bp4m_trace* tr, cudaStream_t st, const Stage2* rw = nullptr) {
-    Workspace& w = g->ws;
     // pio: storage of the shared-memory tiers (0 FP64, 1 FP32, 2 FP16, 3 BF16); prec: the
     // arithmetic type of everything else (tables, global tier)
     const int pio = o->precision == BP4M_FP64 ? 0 : o->precision == BP4M_FP32 ? 1 : o->precision;
@@ -458,7 +467,7 @@ int decode_device(bp4m_graph* g, int ty, const uint32_t* synd, int64_t shots, in
             if (b == 0) return fail(BP4M_ECUDA, "B-BP4MF: no launch configuration for a reweighting tier");
             need = std::max(need, b);
         }
-        int rc = ensure_gscratch(g, need);
+        int rc = ensure_gscratch(w, need);
         if (rc) return rc;
         a.gscratch = w.gscratch;
         a.gscratch_bytes = (int64_t)w.gscratch_bytes;
@@ -497,7 +506,7 @@ int decode_device(bp4m_graph* g, int ty, const uint32_t* synd, int64_t shots, in
         int slots = std::min(n_glob, g->num_sms * global_blocks_per_sm(prec, max_s));
         const size_t budget = (size_t)16 << 30;
         while (slots > 1 && (size_t)slots * slot_bytes > budget) --slots;
-        int rc = ensure_gscratch(g, (size_t)slots * slot_bytes);
+        int rc = ensure_gscratch(w, (size_t)slots * slot_bytes);
         if (rc) return rc;
         a.list = w.lists + (size_t)kGlobalTier * shots;
         a.count = w.small + kGlobalTier;
@@ -514,11 +523,10 @@ int decode_device(bp4m_graph* g, int ty, const uint32_t* synd, int64_t shots, in
 }
 
 // B-BP4MF on device-resident syndromes of both types (type 1 = X-checks, type 0 = Z-checks).
-int bbp4mf_device(bp4m_graph* g, const uint32_t* synd0, const uint32_t* synd1, int64_t shots, int T,
+int bbp4mf_device(bp4m_graph* g, Workspace& w, const uint32_t* synd0, const uint32_t* synd1, int64_t shots, int T,
                   const bp4m_opts* o, uint8_t* obs_pred, uint8_t* flags, int16_t* iters, cudaStream_t st) {
-    int rc = ensure_qbp_ws(g, shots);
+    int rc = ensure_qbp_ws(g, w, shots);
     if (rc) return rc;
-    Workspace& w = g->ws;
     const int prec = o->precision == BP4M_FP64 ? 0 : 1;
     QbpArgs q;
     q.shots = shots;
@@ -554,7 +562,7 @@ int bbp4mf_device(bp4m_graph* g, const uint32_t* synd0, const uint32_t* synd1, i
         s2.skip_iters = w.qiters;
         s2.post = w.post + (size_t)ty * shots * g->host.n_units;
         o2.type = ty;
-        rc = decode_device(g, ty, ty == 0 ? synd0 : synd1, shots, T, &o2, obs_pred + (size_t)ty * shots,
+        rc = decode_device(g, w, ty, ty == 0 ? synd0 : synd1, shots, T, &o2, obs_pred + (size_t)ty * shots,
                            flags + (size_t)ty * shots, iters + (size_t)ty * shots, nullptr, st, &s2);
         if (rc) return rc;
     }
@@ -618,7 +626,367 @@ constexpr int64_t kBatch = (int64_t)1 << 20;
 
 }  // namespace
 
+// ------------------------------------------------------------------ decoding service
+//
+// A request loop over device-resident graphs: callers submit batches of syndromes (host
+// buffers) for any registered graph; worker threads, one per slot, each with its own CUDA
+// stream and per-graph workspaces, take the oldest pending request and merge into it every
+// pending request of the same graph and options that still fits (continuous batching).  The
+// slots' copies and kernels overlap on the device.  A workspace is created the first time a
+// slot decodes a graph; when the device bytes of all workspaces would exceed the budget, the
+// slot frees its least recently used workspaces first, and a request whose workspace cannot
+// fit at all fails with BP4M_ENOMEM.
+
+struct bp4m_server;
+
+namespace {
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct SrvRequest {
+    int64_t id = 0;
+    int graph = 0;
+    int iters = 0;
+    bp4m_opts opts{};
+    int64_t shots = 0;
+    std::vector<uint32_t> synd;  // [shots][n_words], copied at submission
+    uint8_t* out_obs = nullptr;
+    uint8_t* out_conv = nullptr;
+    double t_submit = 0, t_start = 0, t_done = 0;
+    int64_t batch_shots = 0;
+    int slot = -1;
+    int rc = 0;
+    std::string err;
+    bool done = false;
+};
+
+struct SrvSlot {
+    int index = 0;
+    cudaStream_t st = nullptr;
+    std::map<int, Workspace> ws;          // graph id -> workspace
+    std::map<int, int64_t> last_use;      // graph id -> batch counter
+    uint32_t* h_in = nullptr;             // pinned staging
+    uint8_t* h_out = nullptr;             // [2][cap] obs, flags
+    int64_t h_cap = 0, h_words = 0;
+    std::thread th;
+};
+
+size_t ws_bytes(const Workspace& w) {
+    return (size_t)w.cap * (w.words_total * 4 + 5 * w.n_types) + (size_t)w.cap * kTiers * 4 + w.gscratch_bytes;
+}
+
+bool same_batch(const SrvRequest& a, const SrvRequest& b) {
+    return a.graph == b.graph && a.iters == b.iters && a.opts.precision == b.opts.precision &&
+           a.opts.early_exit == b.opts.early_exit && a.opts.decoder == b.opts.decoder &&
+           a.opts.alpha == b.opts.alpha && a.opts.type == b.opts.type;
+}
+
+}  // namespace
+
+struct bp4m_server {
+    std::vector<bp4m_graph*> graphs;
+    int device = -1;
+    int64_t max_batch = 4096;
+    int64_t budget = 0;
+    std::atomic<int64_t> used{0};
+    std::mutex mu;
+    std::condition_variable cv, done_cv;
+    std::deque<SrvRequest*> pending;
+    std::unordered_map<int64_t, SrvRequest*> reqs;
+    int64_t next_id = 0;
+    bool stop = false;
+    std::vector<SrvSlot*> slots;
+    // statistics
+    int64_t n_batches = 0, n_merged = 0, shots_done = 0, evictions = 0, max_inflight = 0;
+    int inflight = 0;
+};
+
+namespace {
+
+int srv_run_batch(bp4m_server* S, SrvSlot& sl, std::vector<SrvRequest*>& batch, int64_t n, int64_t stamp) {
+    SrvRequest& h = *batch[0];
+    bp4m_graph* g = S->graphs[h.graph];
+    const int ty = g->host.n_types == 2 ? h.opts.type : 0;
+    const int nw = n_words_of(g, ty);
+    cudaStream_t st = sl.st;
+    // workspace of this graph in this slot, within the device-memory budget
+    auto it = sl.ws.find(h.graph);
+    const size_t before = it == sl.ws.end() ? 0 : ws_bytes(it->second);
+    Workspace& w = sl.ws[h.graph];
+    sl.last_use[h.graph] = stamp;
+    if (w.cap < n && S->budget > 0) {
+        // bytes of the per-shot buffers at capacity n (ensure_ws) beyond what this workspace holds
+        size_t words = 0;
+        for (int t = 0; t < g->host.n_types; ++t) words += n_words_of(g, t);
+        const int64_t need = (int64_t)((size_t)n * (words * 4 + 5 * g->host.n_types + kTiers * 4)) - (int64_t)before;
+        while (S->used.load() + need > S->budget) {
+            int victim = -1;
+            int64_t oldest = INT64_MAX;
+            for (auto& kv : sl.ws)
+                if (kv.first != h.graph && sl.last_use[kv.first] < oldest) {
+                    oldest = sl.last_use[kv.first];
+                    victim = kv.first;
+                }
+            if (victim < 0) return fail(BP4M_ENOMEM, "the batch's workspace does not fit the device budget");
+            S->used -= (int64_t)ws_bytes(sl.ws[victim]);
+            free_ws(sl.ws[victim]);
+            sl.ws.erase(victim);
+            sl.last_use.erase(victim);
+            std::lock_guard<std::mutex> lk(S->mu);
+            ++S->evictions;
+        }
+    }
+    int rc = ensure_ws(g, w, std::max<int64_t>(n, w.cap));
+    if (rc) return rc;
+    // pinned staging
+    if (sl.h_cap < n || sl.h_words < nw) {
+        cudaFreeHost(sl.h_in);
+        cudaFreeHost(sl.h_out);
+        sl.h_in = nullptr;
+        sl.h_out = nullptr;
+        sl.h_cap = 0;
+        const int64_t cap = std::max<int64_t>(n, S->max_batch);
+        const int64_t words = std::max<int64_t>(nw, sl.h_words);
+        CK(cudaMallocHost(reinterpret_cast<void**>(&sl.h_in), (size_t)cap * words * 4));
+        CK(cudaMallocHost(reinterpret_cast<void**>(&sl.h_out), (size_t)cap * 2));
+        sl.h_cap = cap;
+        sl.h_words = words;
+    }
+    int64_t off = 0;
+    for (SrvRequest* r : batch) {
+        std::memcpy(sl.h_in + (size_t)off * nw, r->synd.data(), (size_t)r->shots * nw * 4);
+        off += r->shots;
+    }
+    CK(cudaMemcpyAsync(w.synd, sl.h_in, (size_t)n * nw * 4, cudaMemcpyHostToDevice, st));
+    rc = decode_device(g, w, ty, w.synd, n, h.iters, &h.opts, w.obs_pred, w.flags, w.iters, nullptr, st);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(sl.h_out, w.obs_pred, (size_t)n, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(sl.h_out + n, w.flags, (size_t)n, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    S->used += (int64_t)ws_bytes(w) - (int64_t)before;
+    off = 0;
+    for (SrvRequest* r : batch) {
+        std::memcpy(r->out_obs, sl.h_out + off, (size_t)r->shots);
+        if (r->out_conv)
+            for (int64_t k = 0; k < r->shots; ++k) r->out_conv[k] = (uint8_t)(sl.h_out[n + off + k] & F_CONVERGED);
+        off += r->shots;
+    }
+    return BP4M_OK;
+}
+
+void srv_worker(bp4m_server* S, SrvSlot* sl) {
+    tl_no_prof = true;
+    cudaSetDevice(S->device);
+    int64_t stamp = 0;
+    for (;;) {
+        std::vector<SrvRequest*> batch;
+        int64_t n = 0;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv.wait(lk, [&] { return S->stop || !S->pending.empty(); });
+            if (S->pending.empty()) return;  // stop requested and nothing left
+            SrvRequest* h = S->pending.front();
+            S->pending.pop_front();
+            batch.push_back(h);
+            n = h->shots;
+            for (auto it = S->pending.begin(); it != S->pending.end();) {
+                SrvRequest* r = *it;
+                if (same_batch(*h, *r) && n + r->shots <= S->max_batch) {
+                    batch.push_back(r);
+                    n += r->shots;
+                    it = S->pending.erase(it);
+                } else {
+                    ++it;
+                }
+            }
+            ++S->inflight;
+            S->max_inflight = std::max<int64_t>(S->max_inflight, S->inflight);
+        }
+        const double t0 = now_s();
+        for (SrvRequest* r : batch) r->t_start = t0;
+        const int rc = srv_run_batch(S, *sl, batch, n, ++stamp);
+        const double t1 = now_s();
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            --S->inflight;
+            ++S->n_batches;
+            S->n_merged += (int64_t)batch.size() - 1;
+            if (rc == BP4M_OK) S->shots_done += n;
+            for (SrvRequest* r : batch) {
+                r->t_done = t1;
+                r->batch_shots = n;
+                r->slot = sl->index;
+                r->rc = rc;
+                if (rc) r->err = g_last_error;
+                r->done = true;
+                std::vector<uint32_t>().swap(r->synd);
+            }
+        }
+        S->done_cv.notify_all();
+    }
+}
+
+}  // namespace
+
 extern "C" {
+
+bp4m_server* bp4m_server_create(int n_slots, int64_t max_batch_shots, int64_t device_budget_bytes) {
+    if (n_slots < 1 || n_slots > 64) {
+        fail(BP4M_EINVAL, "n_slots must be in [1, 64]");
+        return nullptr;
+    }
+    if (max_batch_shots < 1 || max_batch_shots > kBatch) {
+        fail(BP4M_EINVAL, "max_batch_shots must be in [1, 2^20]");
+        return nullptr;
+    }
+    if (device_budget_bytes < 0) {
+        fail(BP4M_EINVAL, "device_budget_bytes must be >= 0 (0: no limit)");
+        return nullptr;
+    }
+    bp4m_server* S = new (std::nothrow) bp4m_server();
+    if (!S) {
+        fail(BP4M_ENOMEM, "out of host memory");
+        return nullptr;
+    }
+    S->max_batch = max_batch_shots;
+    S->budget = device_budget_bytes;
+    if (cudaGetDevice(&S->device) != cudaSuccess) {
+        delete S;
+        fail(BP4M_ECUDA, "no CUDA device");
+        return nullptr;
+    }
+    for (int k = 0; k < n_slots; ++k) {
+        SrvSlot* sl = new SrvSlot();
+        sl->index = k;
+        if (cudaStreamCreateWithFlags(&sl->st, cudaStreamNonBlocking) != cudaSuccess) {
+            delete sl;
+            bp4m_server_destroy(S);
+            fail(BP4M_ECUDA, "cudaStreamCreate failed");
+            return nullptr;
+        }
+        S->slots.push_back(sl);
+    }
+    for (SrvSlot* sl : S->slots) sl->th = std::thread(srv_worker, S, sl);
+    return S;
+}
+
+int bp4m_server_add_graph(bp4m_server* S, bp4m_graph* g) {
+    if (!S || !g) return fail(BP4M_EINVAL, "null argument");
+    int rc = ensure_uploaded(g);
+    if (rc) return rc;
+    if (g->device != S->device) return fail(BP4M_EINVAL, "graph lives on another device");
+    for (int prec = 0; prec < 4; ++prec)
+        if (!g->prepared[prec]) {
+            CK(prepare_decode_kernels(prec));
+            g->prepared[prec] = true;
+        }
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->graphs.push_back(g);
+    return (int)S->graphs.size() - 1;
+}
+
+int64_t bp4m_server_submit(bp4m_server* S, int graph_id, const uint32_t* syndromes, int64_t shots, int iters,
+                           const bp4m_opts* opts, uint8_t* obs_pred, uint8_t* converged) {
+    if (!S || !syndromes || !obs_pred) return fail(BP4M_EINVAL, "null argument");
+    bp4m_graph* g;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (graph_id < 0 || graph_id >= (int)S->graphs.size()) return fail(BP4M_EINVAL, "unknown graph id");
+        g = S->graphs[graph_id];
+    }
+    int rc = check_opts(g, opts, iters);
+    if (rc) return rc;
+    if (opts->decoder == BP4M_DEC_BBP4MF) return fail(BP4M_EUNSUPPORTED, "the service decodes BP4M and BP4MF");
+    if (shots < 1 || shots > kBatch) return fail(BP4M_EINVAL, "shots must be in [1, 2^20]");
+    if (is_device_ptr(syndromes) || is_device_ptr(obs_pred) || (converged && is_device_ptr(converged)))
+        return fail(BP4M_EINVAL, "the service takes host buffers");
+    const int ty = g->host.n_types == 2 ? opts->type : 0;
+    const int nw = n_words_of(g, ty);
+    SrvRequest* r = new (std::nothrow) SrvRequest();
+    if (!r) return fail(BP4M_ENOMEM, "out of host memory");
+    r->graph = graph_id;
+    r->iters = iters;
+    r->opts = *opts;
+    r->shots = shots;
+    r->synd.assign(syndromes, syndromes + (size_t)shots * nw);
+    r->out_obs = obs_pred;
+    r->out_conv = converged;
+    r->t_submit = now_s();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->stop) {
+            delete r;
+            return fail(BP4M_EINVAL, "server is shutting down");
+        }
+        r->id = S->next_id++;
+        S->reqs[r->id] = r;
+        S->pending.push_back(r);
+    }
+    S->cv.notify_one();
+    return r->id;
+}
+
+int bp4m_server_wait(bp4m_server* S, int64_t request, double timeout_s, bp4m_request_info* info) {
+    if (!S) return fail(BP4M_EINVAL, "null server");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(request);
+    if (it == S->reqs.end()) return fail(BP4M_EINVAL, "unknown or already collected request");
+    SrvRequest* r = it->second;
+    const auto pred = [&] { return r->done; };
+    if (timeout_s < 0)
+        S->done_cv.wait(lk, pred);
+    else if (!S->done_cv.wait_for(lk, std::chrono::duration<double>(timeout_s), pred))
+        return fail(BP4M_ETIMEOUT, "request not finished");
+    if (info) {
+        info->t_submit = r->t_submit;
+        info->t_start = r->t_start;
+        info->t_done = r->t_done;
+        info->latency_s = r->t_done - r->t_submit;
+        info->batch_shots = r->batch_shots;
+        info->slot = r->slot;
+    }
+    const int rc = r->rc;
+    const std::string err = r->err;
+    S->reqs.erase(it);
+    delete r;
+    return rc ? fail(rc, err) : BP4M_OK;
+}
+
+int bp4m_server_stats(bp4m_server* S, bp4m_server_stats_t* out) {
+    if (!S || !out) return fail(BP4M_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(S->mu);
+    out->batches = S->n_batches;
+    out->merged_requests = S->n_merged;
+    out->shots = S->shots_done;
+    out->evictions = S->evictions;
+    out->max_inflight_batches = S->max_inflight;
+    out->pending = (int64_t)S->pending.size();
+    out->device_bytes = S->used.load();
+    return BP4M_OK;
+}
+
+int bp4m_server_destroy(bp4m_server* S) {
+    if (!S) return BP4M_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    for (SrvSlot* sl : S->slots)
+        if (sl->th.joinable()) sl->th.join();
+    for (SrvSlot* sl : S->slots) {
+        for (auto& kv : sl->ws) free_ws(kv.second);
+        cudaFreeHost(sl->h_in);
+        cudaFreeHost(sl->h_out);
+        if (sl->st) cudaStreamDestroy(sl->st);
+        delete sl;
+    }
+    for (auto& kv : S->reqs) delete kv.second;
+    delete S;
+    return BP4M_OK;
+}
 
 const char* bp4m_last_error(void) { return g_last_error.c_str(); }
 
@@ -789,7 +1157,7 @@ static int decode_common(bp4m_graph* g, const uint32_t* syndromes, int64_t shots
             CK(cudaMemcpyAsync(w.synd, sd, (size_t)nb * nw * 4, cudaMemcpyHostToDevice, st));
             sd = w.synd;
         }
-        rc = decode_device(g, ty, sd, nb, iters, opts, w.obs_pred, w.flags, w.iters, tr, st);
+        rc = decode_device(g, w, ty, sd, nb, iters, opts, w.obs_pred, w.flags, w.iters, tr, st);
         if (rc) return rc;
         if (tr && tr->flags) CK(cudaMemcpyAsync(tr->flags, w.flags, nb, cudaMemcpyDeviceToDevice, st));
         if (obs_pred) CK(cudaMemcpyAsync(obs_pred + off, w.obs_pred, nb, cudaMemcpyDefault, st));
@@ -854,7 +1222,7 @@ int bp4m_sample_and_decode_range(bp4m_graph* g, uint64_t first_shot, int64_t sho
         rc = sample_into(g, first_shot + (uint64_t)off, nb, seed, stream_id, w.synd, w.obs_true, st);
         if (rc) return rc;
         if (bbp) {
-            rc = bbp4mf_device(g, w.synd, w.synd + (size_t)nb * n_words_of(g, 0), nb, iters, opts, w.obs_pred,
+            rc = bbp4mf_device(g, w, w.synd, w.synd + (size_t)nb * n_words_of(g, 0), nb, iters, opts, w.obs_pred,
                                w.flags, w.iters, st);
             if (rc) return rc;
             ProfScope ps(g, PROF_COUNT, st);
@@ -866,7 +1234,7 @@ int bp4m_sample_and_decode_range(bp4m_graph* g, uint64_t first_shot, int64_t sho
         for (int ty = 0; ty < nt; ++ty) {
             bp4m_opts o = *opts;
             o.type = ty;
-            rc = decode_device(g, ty, w.synd + (size_t)nb * woff, nb, iters, &o, w.obs_pred + (size_t)ty * nb,
+            rc = decode_device(g, w, ty, w.synd + (size_t)nb * woff, nb, iters, &o, w.obs_pred + (size_t)ty * nb,
                                w.flags + (size_t)ty * nb, w.iters + (size_t)ty * nb, nullptr, st);
             if (rc) return rc;
             woff += n_words_of(g, ty);
@@ -914,7 +1282,7 @@ int bp4m_decode_bbp4mf(bp4m_graph* g, const uint32_t* syndromes, int64_t shots, 
         CK(cudaMemcpyAsync(w.synd + (size_t)nb * nw0, syndromes + (size_t)shots * nw0 + (size_t)off * nw1,
                            (size_t)nb * nw1 * 4, cudaMemcpyDefault, st));
         CK(cudaMemsetAsync(w.ctr, 0, C_NUM * sizeof(unsigned long long), st));
-        rc = bbp4mf_device(g, w.synd, w.synd + (size_t)nb * nw0, nb, iters, &o, w.obs_pred, w.flags, w.iters, st);
+        rc = bbp4mf_device(g, w, w.synd, w.synd + (size_t)nb * nw0, nb, iters, &o, w.obs_pred, w.flags, w.iters, st);
         if (rc) return rc;
         for (int ty = 0; ty < 2; ++ty) {
             CK(cudaMemcpyAsync(obs_pred + (size_t)ty * shots + off, w.obs_pred + (size_t)ty * nb, nb,

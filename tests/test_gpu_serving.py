@@ -1,0 +1,130 @@
+"""The decoding service (bp4m_server_*): requests of mixed graphs submitted together give,
+request by request, exactly what bp4m_decode_batch gives each of them alone; compatible
+pending requests are merged into batches; the slots' batches overlap; the device budget
+evicts workspaces or refuses a batch that cannot fit."""
+import numpy as np
+import pytest
+
+import paper_2603_05381_gb300 as pkg
+
+from gpu_util import gpu_sample, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+T = 30
+
+
+def _host_syndromes(g, shots, seed, ty=0):
+    (synds), obs = gpu_sample(g, 0, shots, seed=seed)
+    return synds[ty].cpu().numpy().view(np.uint32).copy()
+
+
+def _alone(g, synd, opts):
+    n = synd.shape[0]
+    pred = np.empty(n, dtype=np.uint8)
+    conv = np.empty(n, dtype=np.uint8)
+    its = np.empty(n, dtype=np.int16)
+    g.decode_batch(synd, T, opts, pred, conv, its)
+    return pred, conv
+
+
+@pytest.fixture(scope="module")
+def graphs():
+    torch_cuda()
+    gs = [pkg.Graph(5, "circuit", 0.006), pkg.Graph(9, "circuit", 0.005), pkg.Graph(7, "code_capacity", 0.08)]
+    yield gs
+    for g in gs:
+        g.close()
+
+
+def test_mixed_requests_match_decode_alone(graphs):
+    rng = np.random.default_rng(3)
+    pools = []
+    for k, g in enumerate(graphs):
+        ty = 1 if k == 2 else 0
+        synd = _host_syndromes(g, 6000, seed=20 + k, ty=ty)
+        opts = pkg.make_opts(precision="fp32" if k != 1 else "fp16", early_exit=True, type=ty)
+        pools.append((g, synd, opts))
+    srv = pkg.Server(slots=3, max_batch_shots=4096)
+    ids = [srv.add_graph(g) for g, _, _ in pools]
+    reqs = []
+    # three large requests occupy the slots, then many small ones queue up behind them
+    for k in range(3):
+        g, synd, opts = pools[1]
+        a = 2000 * k
+        reqs.append((1, a, 2000))
+    for _ in range(60):
+        k = int(rng.integers(0, 3))
+        n = int(rng.integers(1, 300))
+        a = int(rng.integers(0, 6000 - n))
+        reqs.append((k, a, n))
+    outs = []
+    rids = []
+    for k, a, n in reqs:
+        g, synd, opts = pools[k]
+        sub = np.ascontiguousarray(synd[a:a + n])
+        pred = np.full(n, 7, dtype=np.uint8)
+        conv = np.full(n, 7, dtype=np.uint8)
+        rids.append(srv.submit(ids[k], sub, T, opts, pred, conv))
+        outs.append((k, sub, pred, conv))
+    infos = [srv.wait(r) for r in rids]
+    st = srv.stats()
+    srv.close()
+    for (k, sub, pred, conv), info in zip(outs, infos):
+        g, _, opts = pools[k]
+        p0, c0 = _alone(g, sub, opts)
+        assert np.array_equal(pred, p0) and np.array_equal(conv, c0)
+        assert info["t_submit"] <= info["t_start"] <= info["t_done"]
+    lat = np.array([i["latency_s"] for i in infos])
+    print("service: %d requests, %d batches, %d merged, max %d batches in flight, latency p50 %.2f ms p99 %.2f ms"
+          % (len(reqs), st["batches"], st["merged_requests"], st["max_inflight_batches"],
+             1e3 * np.percentile(lat, 50), 1e3 * np.percentile(lat, 99)))
+    assert st["shots"] == sum(n for _, _, n in reqs)
+    assert st["merged_requests"] >= 1
+    assert st["max_inflight_batches"] >= 2
+
+
+def test_budget_evicts_and_refuses(graphs):
+    g5, g9 = graphs[0], graphs[1]
+    s5 = _host_syndromes(g5, 2048, seed=41)
+    s9 = _host_syndromes(g9, 2048, seed=42)
+    opts = pkg.make_opts(precision="fp32")
+    # per-shot buffers of one 2048-shot workspace of the d = 9 graph: a budget of 1.5 of
+    # them holds one graph at a time, so alternating graphs evicts
+    w9 = 2048 * (s9.shape[1] * 4 + 5 + 9 * 4)
+    srv = pkg.Server(slots=1, max_batch_shots=2048, device_budget_bytes=int(1.5 * w9))
+    a, b = srv.add_graph(g5), srv.add_graph(g9)
+    for rep in range(3):
+        for gid, g, synd in ((a, g5, s5), (b, g9, s9)):
+            pred = np.empty(2048, dtype=np.uint8)
+            srv.wait(srv.submit(gid, synd, T, opts, pred))
+            assert np.array_equal(pred, _alone(g, synd, opts)[0])
+    st = srv.stats()
+    srv.close()
+    print("budget: %d evictions" % st["evictions"])
+    assert st["evictions"] >= 3
+    # a budget below one workspace refuses the batch
+    srv = pkg.Server(slots=1, max_batch_shots=2048, device_budget_bytes=1024)
+    gid = srv.add_graph(g9)
+    pred = np.empty(2048, dtype=np.uint8)
+    rid = srv.submit(gid, s9, T, opts, pred)
+    with pytest.raises(pkg.Bp4mError) as e:
+        srv.wait(rid)
+    assert e.value.code == -2
+    srv.close()
+
+
+def test_rejects_device_buffers_and_bbp4mf(graphs):
+    torch = torch_cuda()
+    g = graphs[0]
+    srv = pkg.Server(slots=1)
+    gid = srv.add_graph(g)
+    nw = g.info()["n_words"][0]
+    dev = torch.zeros((4, nw), dtype=torch.int32, device="cuda")
+    pred = np.empty(4, dtype=np.uint8)
+    with pytest.raises(pkg.Bp4mError):
+        srv.submit(gid, dev, T, pkg.make_opts(), pred)
+    host = np.zeros((4, nw), dtype=np.uint32)
+    with pytest.raises(pkg.Bp4mError):
+        srv.submit(gid, host, T, pkg.make_opts(decoder="bbp4mf"), pred)
+    srv.close()
