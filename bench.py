@@ -219,6 +219,12 @@ def run_serving(args, dev):
     for r in ids:
         srv.wait(r)
     cap_shots = sum(o.shape[0] for _, _, o in burst) / (time.perf_counter() - t0)
+    # the plain form on the same requests: one FP32 bp4m_decode_batch call per request, in order
+    opts32 = pkg.make_opts(precision="fp32", early_exit=True)
+    t0 = time.perf_counter()
+    for k, sy, o in burst:
+        graphs[k].decode_batch(sy, T, opts32, o)
+    plain_shots = sum(o.shape[0] for _, _, o in burst) / (time.perf_counter() - t0)
     mean_req = 2048.5
     rate = args.serve_load * cap_shots / mean_req
     reqs = [make_request() for _ in range(args.serve_requests)]
@@ -242,7 +248,8 @@ def run_serving(args, dev):
     shots = sum(o.shape[0] for _, _, o in reqs)
     return {"graphs": "rotated memory-Z circuit, d in {%s}, p=%g" % (",".join(map(str, ds)), P),
             "requests": len(reqs), "request_shots": "uniform 1..4096", "iters": T, "slots": args.serve_slots,
-            "capacity_shots_per_s": cap_shots, "offered_load": args.serve_load,
+            "capacity_shots_per_s": cap_shots, "plain_fp32_per_request_shots_per_s": plain_shots,
+            "capacity_vs_plain": cap_shots / plain_shots, "offered_load": args.serve_load,
             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "sustained_shots_per_s": shots / wall,
             "batches": st["batches"] - st0["batches"], "merged_requests": st["merged_requests"] - st0["merged_requests"],
