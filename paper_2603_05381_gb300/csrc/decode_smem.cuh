@@ -245,6 +245,11 @@ struct Regs<float, N> {
     }
 };
 
+// 1 if lambda > 0, else 0 (NaN and -0 give 0), on the FMA pipe: saturate(lambda x 2^64).
+// A positive lambda below 2^-64 would give a fraction; such a lambda is a tie by any margin
+// the decoder distinguishes.
+__device__ __forceinline__ float keep_f(float lam) { return __saturatef(__fmul_rn(lam, 0x1p64f)); }
+
 __device__ __forceinline__ float max3f(float a, float b, float c) {
     float r;
     asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
@@ -265,10 +270,11 @@ __device__ __forceinline__ void combine_max(T& m1, T& m2, int& k, T o1, T o2, in
 }
 
 // Blocks per SM the kernel is compiled for: the FP32 384- and 448-thread tiers (96 and 112
-// rows, 79 and 106 KB of shared memory) run two blocks per SM; the others are limited by
-// shared memory or 128 registers.
-__host__ __device__ constexpr int blocks_for(int nt, int elem_bytes) {
-    return (elem_bytes == 4 && (nt == 384 || nt == 448)) ? 2 : min_blocks(nt);
+// rows, 79 and 106 KB of shared memory) run two blocks per SM, and so does the 512-thread
+// tier (128 rows) with 16-bit messages (102 KB); the others are limited by shared memory or
+// 128 registers.
+__host__ __device__ constexpr int blocks_for(int nt, int elem_bytes, int msg_bytes) {
+    return (elem_bytes == 4 && (nt == 384 || nt == 448 || (nt == 512 && msg_bytes == 2))) ? 2 : min_blocks(nt);
 }
 
 // REG = true keeps each thread's own outputs M[i][k] in registers between iterations (no
@@ -277,7 +283,7 @@ __host__ __device__ constexpr int blocks_for(int nt, int elem_bytes) {
 // computed in the block by Dijkstra from every defect over per-qubit weights derived from
 // the first stage's posteriors (instead of being gathered from the static tables).
 template <typename T, int CH, int G, bool TRACE, bool REG, bool RW = false, typename MS = T>
-__global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof(T))) decode_smem_kernel(const DecodeArgs a) {
+__global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof(T), (int)sizeof(MS))) decode_smem_kernel(const DecodeArgs a) {
     constexpr int SMAX = CH * G;
     constexpr int NT = SMAX * G;
     constexpr int R = 32 / G;
@@ -506,6 +512,7 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
         Regs<T, REG ? CH : 2> mo;
         int am_prev = -1;          // REG: argmax column of the previous update and its output
         T out_am = T(0);
+        T out_am_gen = T(0);       // REG, FP32: the generic formula's value held in registers for it
         int t = 0;
         bool any_conv = false, forced_ran = false;
         int out_par = 0, out_forced = 0, out_from_best = 0;
@@ -515,6 +522,7 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
             // ---- read phase: Q = l + M[k][i]/alpha for the next update; for t > 0 the
             // marginalization of lambda^t = l + (M[i][k] + M[k][i])
             Mask bits = 0;
+            float cntf = 0.f;
             if (!wact) {
             } else if (!act) {
 #pragma unroll
@@ -531,9 +539,12 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                         for (int c = 0; c < CH; ++c) q[c] = B2<T>::fma_(RM(c), ainv, RL(c));
                     }
                 } else if constexpr (std::is_same<T, float>::value) {
-                    // two columns per packed instruction; same roundings as the scalar form
+                    // two columns per packed instruction; same roundings as the scalar form.
+                    // The kept count is a sum of keep(lambda) in {0, 1} on the FMA pipe; the
+                    // kept column itself is found only when every row has exactly one
+                    // (row_kept_column below).
                     const float2 ainv2 = make_float2(ainv, ainv);
-                    Mask b0 = 0, b1 = 0;
+                    float2 cnt2 = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int j = 0; j < CH / 2; ++j) {
                         const int c = 2 * j;
@@ -546,23 +557,25 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                             own = make_float2(CM(c), CM(c + 1));
                         q.p[j] = __ffma2_rn(x, ainv2, l);
                         const float2 lam = __fadd2_rn(l, __fadd2_rn(own, x));
-                        b0 |= (Mask)(lam.x > 0.f ? 1u : 0u) << c;
-                        b1 |= (Mask)(lam.y > 0.f ? 1u : 0u) << (c + 1);
+                        cnt2 = __fadd2_rn(cnt2, make_float2(keep_f(lam.x), keep_f(lam.y)));
                         if (tr_on && trl && COL(c) < s)
                             trl[((size_t)shot * a.s_cap + i) * a.s_cap + COL(c)] = lam.x * (float)kLn2;
                         if (tr_on && trl && COL(c + 1) < s)
                             trl[((size_t)shot * a.s_cap + i) * a.s_cap + COL(c + 1)] = lam.y * (float)kLn2;
                     }
-                    bits = b0 | b1;
+                    cntf = cnt2.x + cnt2.y;
                     if (!REG && own_diag) {
-                        const float lam = Lm[i * P + i] + Dg[i];
-                        bits = (bits & ~((Mask)1 << c_diag)) | ((Mask)(lam > 0.f ? 1u : 0u) << c_diag);
+                        // the generic term used Mt[i][i] = 0 on both sides: lambda_ii = l_ii
+                        const float lii = Lm[i * P + i];
+                        const float lam = lii + Dg[i];
+                        cntf += keep_f(lam) - keep_f(lii + (0.f + 0.f));
                         if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + i] = lam * (float)kLn2;
                     }
                     if (REG && owner_of<PAIR, G>(am_prev) == g) {
-                        const int ca = reg_of<PAIR, G>(am_prev);
-                        const float lam = Lm[i * P + am_prev] + (out_am + IO::ld(Mt + i * PM + am_prev));
-                        bits = (bits & ~((Mask)1 << ca)) | ((Mask)(lam > 0.f ? 1u : 0u) << ca);
+                        // the register copy of the argmax column holds the generic output
+                        const float l = Lm[i * P + am_prev], x = IO::ld(Mt + i * PM + am_prev);
+                        const float lam = l + (out_am + x);
+                        cntf += keep_f(lam) - keep_f(l + (out_am_gen + x));
                         if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + am_prev] = lam * (float)kLn2;
                     }
                 } else {
@@ -597,15 +610,54 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                     }
                 }
             }
-            // kept count << 16 plus (first kept column + 1), summed over the row's G threads:
-            // the count is exact, the column is the row's only kept one when the count is 1
-            int pk = ((sizeof(Mask) == 8 ? __popcll((unsigned long long)bits) : __popc((unsigned)bits)) << 16) +
-                     (bits ? COL((sizeof(Mask) == 8 ? __ffsll((long long)bits) : __ffs((int)bits)) - 1) + 1 : 0);
+            int cnt, chosen = -1;
+            if constexpr (std::is_same<T, float>::value) {
 #pragma unroll
-            for (int off = R; off < 32; off <<= 1) pk += __shfl_xor_sync(kFull, pk, off);
-            const int cnt = pk >> 16;
-            const int chosen = (pk & 0xFFFF) - 1;
+                for (int off = R; off < 32; off <<= 1) cntf += __shfl_xor_sync(kFull, cntf, off);
+                cnt = (int)cntf;
+            } else {
+                // kept count << 16 plus (first kept column + 1), summed over the row's G threads:
+                // the count is exact, the column is the row's only kept one when the count is 1
+                int pk = ((sizeof(Mask) == 8 ? __popcll((unsigned long long)bits) : __popc((unsigned)bits)) << 16) +
+                         (bits ? COL((sizeof(Mask) == 8 ? __ffsll((long long)bits) : __ffs((int)bits)) - 1) + 1 : 0);
+#pragma unroll
+                for (int off = R; off < 32; off <<= 1) pk += __shfl_xor_sync(kFull, pk, off);
+                cnt = pk >> 16;
+                chosen = (pk & 0xFFFF) - 1;
+            }
             const int conv = __syncthreads_and(t > 0 && (!act || cnt == 1));
+            if constexpr (std::is_same<T, float>::value) {
+                if (conv && wact) {
+                    // every row keeps exactly one variable: find it (the same lambdas as above)
+                    int k1 = -1;
+                    if (act) {
+#pragma unroll
+                        for (int j = 0; j < CH / 2; ++j) {
+                            const int c = 2 * j;
+                            const float2 l = RL2(j);
+                            const float2 x = RM2(j);
+                            float2 own;
+                            if constexpr (REG)
+                                own = mo.p[j];
+                            else
+                                own = make_float2(CM(c), CM(c + 1));
+                            float2 lam = __fadd2_rn(l, __fadd2_rn(own, x));
+                            if (!REG && own_diag && c == c_diag) lam.x = Lm[i * P + i] + Dg[i];
+                            if (!REG && own_diag && c + 1 == c_diag) lam.y = Lm[i * P + i] + Dg[i];
+                            if (REG && owner_of<PAIR, G>(am_prev) == g) {
+                                const float fix = Lm[i * P + am_prev] + (out_am + IO::ld(Mt + i * PM + am_prev));
+                                if (c == reg_of<PAIR, G>(am_prev)) lam.x = fix;
+                                if (c + 1 == reg_of<PAIR, G>(am_prev)) lam.y = fix;
+                            }
+                            if (lam.x > 0.f) k1 = COL(c);
+                            if (lam.y > 0.f) k1 = COL(c + 1);
+                        }
+                    }
+#pragma unroll
+                    for (int off = R; off < 32; off <<= 1) k1 = max(k1, __shfl_xor_sync(kFull, k1, off));
+                    chosen = k1;
+                }
+            }
 
             if (t > 0) {
                 bool have_cand = false, cand_forced = false;
@@ -856,6 +908,13 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                     if (REG) {
                         am_prev = am;
                         out_am = oam;
+                        if constexpr (std::is_same<T, float>::value) {
+                            // what the packed output loop wrote for the argmax column: u = ex2(0)
+                            const float u0 = B2<float>::ex2(0.f);
+                            float og = __fmaf_rn(B2<float>::lg2(__fmaf_rn(-cf, u0, Aa)), -1.f, -m1);
+                            if constexpr (HALF) og = IO::unpack(IO::pack(og, 0.f)).x;
+                            out_am_gen = og;
+                        }
                     }
                     if (own_diag) {
                         if (!REG) Dg[i] = IO::ld(Mt + i * PM + i);

@@ -18,7 +18,8 @@ cudaError_t dispatch_half(int tier, const DecodeArgs& a, int num_sms, cudaStream
         case 2: return run_tier2<float, 32, 2, kReg32[2], MS>(a, num_sms, st, prep);
         case 3: return run_tier2<float, 24, 4, kReg32[3], MS>(a, num_sms, st, prep);
         case 4: return run_tier2<float, 28, 4, kReg32[4], MS>(a, num_sms, st, prep);
-        case 5: return run_tier2<float, 32, 4, kReg32[5], MS>(a, num_sms, st, prep);
+        // 128 rows: two blocks per SM without register-cached outputs (64 registers)
+        case 5: return run_tier2<float, 32, 4, false, MS>(a, num_sms, st, prep);
         case 6: return run_tier2<float, 36, 4, kReg32[6], MS>(a, num_sms, st, prep);
         case 7: return run_tier2<float, 40, 4, kReg32[7], MS>(a, num_sms, st, prep);
         default: return cudaErrorInvalidValue;
