@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--serve-load", type=float, default=0.5)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--no-serve", action="store_true")
+    # fused multi-graph decode of circuit and code-capacity graphs (d = 5, 9, 13, 17) with
+    # uneven shot counts, FP16/BF16/FP32 messages against the plain per-graph FP32 form
+    ap.add_argument("--fused", action="store_true")
+    ap.add_argument("--fused-scale", type=float, default=1.0)
     return ap.parse_args()
 
 
@@ -256,6 +260,73 @@ def run_serving(args, dev):
             "max_inflight_batches": st["max_inflight_batches"]}
 
 
+def run_fused(args, dev):
+    """Fused decode (Multi) over circuit (p = 0.005) and code-capacity (p = 0.10, X type)
+    graphs of d = 5, 9, 13, 17 with uneven shot counts drawn from {1e5, 2.5e5, 5e5, 1e6}
+    (seed 7, scaled by --fused-scale), T = 50, against one bp4m_decode_batch call per graph
+    in FP32.  Shots/s of each form; outputs must agree with the FP32 plain form on the
+    recorded fraction of shots."""
+    import numpy as np
+    import torch
+    import paper_2603_05381_gb300 as pkg
+
+    rng = np.random.default_rng(7)
+    specs = [(m, d) for d in (5, 9, 13, 17) for m in ("circuit", "code_capacity")]
+    counts = [int(args.fused_scale * rng.choice([100000, 250000, 500000, 1000000])) for _ in specs]
+    graphs, synds = [], []
+    for (model, d), n in zip(specs, counts):
+        g = pkg.Graph(d, model, 0.005 if model == "circuit" else 0.10)
+        info = g.info()
+        words = sum(info["n_words"])
+        sy = torch.empty((n * words,), dtype=torch.int32, device=dev)
+        ob = torch.empty((info["n_types"], n), dtype=torch.uint8, device=dev)
+        g.sample(sy, ob, first_shot=0, seed=SEED)
+        nw = info["n_words"][0]
+        synds.append(sy[:n * nw].view(n, nw).cpu().numpy().view(np.uint32).copy())
+        graphs.append(g)
+        del sy, ob
+    torch.cuda.synchronize()
+    total = sum(counts)
+    out = {"graphs": "rotated circuit p=0.005 and code-capacity p=0.10 (X), d in {5,9,13,17}", "shots": counts,
+           "iters": T}
+    # plain: one FP32 decode_batch per graph
+    opts32 = pkg.make_opts(precision="fp32")
+    plain = []
+    for g, sy in zip(graphs, synds):   # warm
+        g.decode_batch(sy[:1024], T, opts32, np.empty(1024, dtype=np.uint8))
+    t0 = time.perf_counter()
+    per_graph = []
+    for (model, d), g, sy in zip(specs, graphs, synds):
+        o = np.empty(sy.shape[0], dtype=np.uint8)
+        t1 = time.perf_counter()
+        g.decode_batch(sy, T, opts32, o)
+        per_graph.append({"graph": "%s d=%d" % (model, d), "shots": int(sy.shape[0]),
+                          "ms": 1e3 * (time.perf_counter() - t1)})
+        plain.append(o)
+    out["plain_fp32_shots_per_s"] = total / (time.perf_counter() - t0)
+    out["plain_fp32_per_graph"] = per_graph
+    # the largest defect count of the batch sizes the streaming tier (64-column steps)
+    max_s = max(int(np.unpackbits(sy.view(np.uint8), axis=1).sum(axis=1).max()) for sy in synds)
+    out["max_defects"] = max(161, min(1024, max_s))
+    for prec in ("fp32", "fp16", "bf16"):
+        m = pkg.Multi(graphs, counts, T, pkg.make_opts(precision=prec), max_defects=out["max_defects"])
+        outs = [np.empty(n, dtype=np.uint8) for n in counts]
+        m.run(synds, outs)          # autotuner
+        m.run(synds, outs)          # capture
+        t0 = time.perf_counter()
+        m.run(synds, outs)          # replay
+        dt = time.perf_counter() - t0
+        info = m.info()
+        m.close()
+        agree = sum(int((o == p).sum()) for o, p in zip(outs, plain)) / total
+        out[prec] = {"shots_per_s": total / dt, "vs_plain_fp32": total / dt / out["plain_fp32_shots_per_s"],
+                     "outputs_equal_to_fp32_plain": agree, "tier_plan": info["plan"],
+                     "plan_ms": info["plan_ms"]}
+    for g in graphs:
+        g.close()
+    return out
+
+
 def run_ours(args, rank, world, local):
     import numpy as np
     import torch
@@ -402,6 +473,8 @@ def run_ours(args, rank, world, local):
     }
     if rank == 0 and not args.no_serve:
         line["serving"] = run_serving(args, dev)
+    if rank == 0 and args.fused:
+        line["fused"] = run_fused(args, dev)
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if world > 1:

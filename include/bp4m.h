@@ -303,6 +303,40 @@ int bp4m_server_stats(bp4m_server* s, bp4m_server_stats_t* out);
 /* Finishes the queued requests, stops the workers and frees the service's device memory. */
 int bp4m_server_destroy(bp4m_server* s);
 
+/* ---- Fused decode of several graphs (no counterpart in the paper: batching of the BP4M
+   decode of Sec. "Belief Propagation" across graphs).
+
+   n graphs (a code-capacity graph with its Pauli type in types[k]; types may be NULL for
+   type 0) are decoded together: each graph's syndromes are classified into shared tier
+   lists and every decode tier is one persistent launch over the shots of all graphs, so
+   uneven distances and shot counts share the GPU in one pass.  bp4m_multi_create
+   allocates device buffers for max_shots[k] shots per graph (< 2^21) and pinned staging.
+   The first bp4m_multi_run times each candidate tier plan on its shots and keeps the
+   fastest (autotuner; that run decodes six times); later runs with use_cuda_graph capture
+   the whole run (copies, classification, tier launches, streaming tier, copies back) once
+   per shot vector in a CUDA graph and replay it.  Results equal bp4m_decode_batch of each
+   graph.  FP32, FP16 or BF16 messages; BP4M or BP4MF.  Shots with more than max_defects
+   (161..1024) unsatisfied detectors are not decoded and make the run return
+   BP4M_EUNSUPPORTED.  Not thread-safe per plan. */
+typedef struct bp4m_multi bp4m_multi;
+
+typedef struct {
+    int plan;             /* index of the chosen tier plan */
+    double plan_ms[3];    /* autotuner timings of the candidate plans (ms) */
+    int64_t runs;         /* completed runs */
+    int64_t graph_replays;/* runs replayed from the captured CUDA graph */
+    uint64_t msg_updates; /* message updates of the last run */
+} bp4m_multi_info_t;
+
+bp4m_multi* bp4m_multi_create(int n, bp4m_graph* const* graphs, const int* types, const int64_t* max_shots,
+                              int iters, const bp4m_opts* opts, int max_defects, int use_cuda_graph);
+/* syndromes[k]: host uint32 [shots[k]][n_words]; obs_pred[k] / converged[k] (may be NULL):
+   host uint8 [shots[k]].  Synchronous. */
+int bp4m_multi_run(bp4m_multi* m, const uint32_t* const* syndromes, const int64_t* shots, uint8_t* const* obs_pred,
+                   uint8_t* const* converged);
+int bp4m_multi_info(const bp4m_multi* m, bp4m_multi_info_t* out);
+void bp4m_multi_destroy(bp4m_multi* m);
+
 const char* bp4m_last_error(void);
 
 /* Library version string. */

@@ -221,3 +221,47 @@ class Server:
         except Exception:
             pass
 
+
+class Multi:
+    """Fused decode of several graphs (bp4m_multi_*): one launch per decode tier over the
+    shots of all graphs, autotuned tier plan, CUDA-graph replay.  Host numpy buffers."""
+
+    def __init__(self, graphs, max_shots, iters, opts, types=None, max_defects=256, cuda_graph=True):
+        lib = load()
+        n = len(graphs)
+        hs = (ctypes.c_void_p * n)(*[g._h.value for g in graphs])
+        caps = (ctypes.c_int64 * n)(*[int(x) for x in max_shots])
+        tys = (ctypes.c_int * n)(*[int(t) for t in (types or [0] * n)])
+        h = lib.bp4m_multi_create(n, hs, tys, caps, int(iters), ctypes.byref(opts), int(max_defects),
+                                  1 if cuda_graph else 0)
+        if not h:
+            raise Bp4mError(-1, lib.bp4m_last_error().decode(errors="replace"))
+        self._h = ctypes.c_void_p(h)
+        self.n = n
+
+    def run(self, syndromes, obs_pred, converged=None):
+        """syndromes[k]: uint32 [shots_k, n_words]; obs_pred[k] (and converged[k]): uint8 [shots_k]."""
+        n = self.n
+        sy = (ctypes.c_void_p * n)(*[_ptr(x) for x in syndromes])
+        sh = (ctypes.c_int64 * n)(*[int(o.shape[0]) for o in obs_pred])
+        ob = (ctypes.c_void_p * n)(*[_ptr(x) for x in obs_pred])
+        cv = (ctypes.c_void_p * n)(*[_ptr(x) for x in converged]) if converged is not None else None
+        check(load().bp4m_multi_run(self._h, sy, sh, ob, cv))
+
+    def info(self):
+        mi = _capi.MultiInfo()
+        check(load().bp4m_multi_info(self._h, ctypes.byref(mi)))
+        return {"plan": mi.plan, "plan_ms": list(mi.plan_ms), "runs": mi.runs, "graph_replays": mi.graph_replays,
+                "msg_updates": mi.msg_updates}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().bp4m_multi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -87,6 +87,11 @@ class ServerStats(ctypes.Structure):
                 ("pending", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
 
 
+class MultiInfo(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_int), ("plan_ms", ctypes.c_double * 3), ("runs", ctypes.c_int64),
+                ("graph_replays", ctypes.c_int64), ("msg_updates", ctypes.c_uint64)]
+
+
 _P = ctypes.c_void_p
 SIGNATURES = {
     "bp4m_build_graph": (ctypes.c_int, [ctypes.POINTER(Code), ctypes.POINTER(Noise), ctypes.POINTER(_P)]),
@@ -114,6 +119,11 @@ SIGNATURES = {
     "bp4m_server_wait": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(RequestInfo)]),
     "bp4m_server_stats": (ctypes.c_int, [_P, ctypes.POINTER(ServerStats)]),
     "bp4m_server_destroy": (ctypes.c_int, [_P]),
+    "bp4m_multi_create": (_P, [ctypes.c_int, _P, _P, _P, ctypes.c_int, ctypes.POINTER(Opts), ctypes.c_int,
+                               ctypes.c_int]),
+    "bp4m_multi_run": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "bp4m_multi_info": (ctypes.c_int, [_P, ctypes.POINTER(MultiInfo)]),
+    "bp4m_multi_destroy": (None, [_P]),
     "bp4m_last_error": (ctypes.c_char_p, []),
     "bp4m_version": (ctypes.c_char_p, []),
 }

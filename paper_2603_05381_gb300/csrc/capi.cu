@@ -830,6 +830,150 @@ void srv_worker(bp4m_server* S, SrvSlot* sl) {
 
 }  // namespace
 
+// ------------------------------------------------------------------ fused multi-graph decode
+//
+// Several graphs (or Pauli types of one graph) decoded together: each graph's syndromes are
+// classified into shared tier lists whose items name the graph (entry << kMultiShift |
+// shot), and every decode tier is one persistent launch over the shots of all graphs.
+// With a fixed shot vector the whole sequence (host-to-device copies from the plan's
+// pinned staging, classification, the tier launches, the streaming tier, device-to-host
+// copies) has no host synchronisation, so it is captured once in a CUDA graph and
+// replayed.  The tier plan (which row counts each tier takes) is chosen by timing the
+// candidates on the first run (the autotuner).
+
+struct bp4m_multi;
+
+namespace {
+
+struct MultiHostEntry {
+    bp4m_graph* g = nullptr;
+    int type = 0;
+    int n_words = 0;
+    int64_t cap = 0;
+    uint32_t* d_synd = nullptr;
+    uint8_t* d_obs = nullptr;
+    uint8_t* d_flags = nullptr;
+    int16_t* d_iters = nullptr;
+    uint32_t* h_synd = nullptr;   // pinned
+    uint8_t* h_out = nullptr;     // pinned [2][cap]: obs, flags
+};
+
+// Candidate tier plans of the autotuner, as the largest row count each FP32 tier takes;
+// a tier whose bound equals the previous one's is never populated.
+constexpr int kPlanCount = 3;
+const int kPlanSmax[kPlanCount][kGlobalTier] = {
+    {0, 32, 64, 96, 112, 128, 144, 160},   // every tier (finest padding)
+    {0, 32, 64, 96, 96, 128, 128, 160},    // 32-row steps above 64
+    {0, 32, 64, 64, 112, 112, 144, 160},   // 48/32-row steps
+};
+
+}  // namespace
+
+struct bp4m_multi {
+    std::vector<MultiHostEntry> e;
+    int device = -1;
+    int num_sms = 0;
+    int iters = 0;
+    bp4m_opts opts{};
+    int pio = 1;
+    int max_defects = 256;
+    int64_t total_cap = 0;
+    MultiEntry* d_entries = nullptr;
+    int32_t* lists = nullptr;
+    int32_t* small = nullptr;          // counts[kTiers], next[kTiers], max_s
+    unsigned long long* ctr = nullptr;
+    unsigned long long* h_ctr = nullptr;
+    void* gscratch = nullptr;
+    size_t gslot_bytes = 0;
+    int gsmax = 0;
+    int gslots = 0;
+    cudaStream_t st = nullptr;
+    int plan = 0;
+    bool tuned = false;
+    double plan_ms[kPlanCount] = {0, 0, 0};
+    bool use_graph = true;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int64_t> graph_shots;  // shot vector the captured graph was made for
+    int64_t runs = 0, replays = 0;
+};
+
+namespace {
+
+void multi_free(bp4m_multi* m) {
+    for (auto& x : m->e) {
+        cudaFree(x.d_synd);
+        cudaFree(x.d_obs);
+        cudaFree(x.d_flags);
+        cudaFree(x.d_iters);
+        cudaFreeHost(x.h_synd);
+        cudaFreeHost(x.h_out);
+    }
+    cudaFree(m->d_entries);
+    cudaFree(m->lists);
+    cudaFree(m->small);
+    cudaFree(m->ctr);
+    cudaFreeHost(m->h_ctr);
+    cudaFree(m->gscratch);
+    if (m->exec) cudaGraphExecDestroy(m->exec);
+    if (m->st) cudaStreamDestroy(m->st);
+    delete m;
+}
+
+// Everything of one run after the host staging is filled; no host synchronisation.
+int multi_enqueue(bp4m_multi* m, const std::vector<int64_t>& shots, int plan) {
+    cudaStream_t st = m->st;
+    const int n = (int)m->e.size();
+    for (int k = 0; k < n; ++k) {
+        const MultiHostEntry& x = m->e[k];
+        if (shots[k] > 0)
+            CK(cudaMemcpyAsync(x.d_synd, x.h_synd, (size_t)shots[k] * x.n_words * 4, cudaMemcpyHostToDevice, st));
+    }
+    CK(cudaMemsetAsync(m->small, 0, (2 * kTiers + 1) * sizeof(int32_t), st));
+    CK(cudaMemsetAsync(m->ctr, 0, C_NUM * sizeof(unsigned long long), st));
+    TierPlan tp{};
+    for (int t = 0; t < kGlobalTier; ++t) tp.smax[t] = m->pio == 0 ? tier_plan(0).smax[t] : kPlanSmax[plan][t];
+    tp.smax[kGlobalTier] = 0x7fffffff;
+    for (int k = 0; k < n; ++k) {
+        const MultiHostEntry& x = m->e[k];
+        CK(launch_classify(x.d_synd, shots[k], x.n_words, tp, m->lists, m->small, m->small + 2 * kTiers, x.d_obs,
+                           x.d_flags, x.d_iters, nullptr, nullptr, nullptr, nullptr, st, m->total_cap,
+                           (int32_t)((int64_t)k << kMultiShift)));
+    }
+    DecodeArgs a;
+    a.multi = m->d_entries;
+    a.T = m->iters;
+    a.early_exit = m->opts.early_exit ? 1 : 0;
+    a.decoder = m->opts.decoder;
+    a.alpha = m->opts.alpha;
+    a.ctr = m->ctr;
+    for (int tier = 1; tier < kGlobalTier; ++tier) {
+        if (m->pio != 0 && tier > 1 && kPlanSmax[plan][tier] == kPlanSmax[plan][tier - 1]) continue;
+        a.list = m->lists + (size_t)tier * m->total_cap;
+        a.count = m->small + tier;
+        a.next = m->small + kTiers + tier;
+        a.tier = tier;
+        CK(launch_decode_tier(m->pio, tier, a, m->num_sms, st));
+    }
+    a.list = m->lists + (size_t)kGlobalTier * m->total_cap;
+    a.count = m->small + kGlobalTier;
+    a.next = m->small + kTiers + kGlobalTier;
+    a.tier = kGlobalTier;
+    a.gscratch = m->gscratch;
+    a.gslot_elems = (int64_t)(m->gslot_bytes / sizeof(float) / 3);
+    a.gsmax = m->gsmax;
+    CK(launch_decode_global(1, a, m->gslots, st));
+    for (int k = 0; k < n; ++k) {
+        const MultiHostEntry& x = m->e[k];
+        if (shots[k] <= 0) continue;
+        CK(cudaMemcpyAsync(x.h_out, x.d_obs, (size_t)shots[k], cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(x.h_out + x.cap, x.d_flags, (size_t)shots[k], cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaMemcpyAsync(m->h_ctr, m->ctr, C_NUM * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    return BP4M_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 bp4m_server* bp4m_server_create(int n_slots, int64_t max_batch_shots, int64_t device_budget_bytes) {
@@ -986,6 +1130,175 @@ int bp4m_server_destroy(bp4m_server* S) {
     for (auto& kv : S->reqs) delete kv.second;
     delete S;
     return BP4M_OK;
+}
+
+bp4m_multi* bp4m_multi_create(int n, bp4m_graph* const* graphs, const int* types, const int64_t* max_shots,
+                              int iters, const bp4m_opts* opts, int max_defects, int use_cuda_graph) {
+    if (n < 1 || n > 1000 || !graphs || !max_shots) {
+        fail(BP4M_EINVAL, "need 1..1000 graphs and their capacities");
+        return nullptr;
+    }
+    if (!opts || (opts->precision != BP4M_FP32 && opts->precision != BP4M_FP16 && opts->precision != BP4M_BF16)) {
+        fail(BP4M_EINVAL, "the fused decode runs in FP32, FP16 or BF16");
+        return nullptr;
+    }
+    if (opts->decoder != BP4M_DEC_BP4M && opts->decoder != BP4M_DEC_BP4MF) {
+        fail(BP4M_EUNSUPPORTED, "the fused decode runs BP4M and BP4MF");
+        return nullptr;
+    }
+    if (max_defects < 161 || max_defects > 1024) {
+        fail(BP4M_EINVAL, "max_defects must be in [161, 1024]");
+        return nullptr;
+    }
+    bp4m_multi* m = new (std::nothrow) bp4m_multi();
+    if (!m) {
+        fail(BP4M_ENOMEM, "out of host memory");
+        return nullptr;
+    }
+    m->iters = iters;
+    m->opts = *opts;
+    m->pio = opts->precision;
+    m->max_defects = max_defects;
+    m->use_graph = use_cuda_graph != 0;
+    std::vector<MultiEntry> host(n);
+    auto bad = [&](int rc) -> bp4m_multi* {
+        multi_free(m);
+        (void)rc;
+        return nullptr;
+    };
+    for (int k = 0; k < n; ++k) {
+        bp4m_graph* g = graphs[k];
+        if (!g) return bad(fail(BP4M_EINVAL, "null graph"));
+        int rc = ensure_uploaded(g);
+        if (rc) return bad(rc);
+        if (k == 0) {
+            m->device = g->device;
+            m->num_sms = g->num_sms;
+        } else if (g->device != m->device) {
+            return bad(fail(BP4M_EINVAL, "graphs on different devices"));
+        }
+        rc = check_opts(g, opts, iters);
+        if (rc) return bad(rc);
+        if (max_shots[k] < 1 || max_shots[k] > kMultiMask) return bad(fail(BP4M_EINVAL, "max_shots must be in [1, 2^21)"));
+        MultiHostEntry x;
+        x.g = g;
+        x.type = g->host.n_types == 2 ? (types ? types[k] : 0) : 0;
+        if (x.type < 0 || x.type >= g->host.n_types) return bad(fail(BP4M_EINVAL, "bad Pauli type"));
+        x.n_words = n_words_of(g, x.type);
+        x.cap = max_shots[k];
+        m->e.push_back(x);
+        MultiHostEntry& y = m->e.back();
+        if (dalloc(&y.d_synd, (size_t)y.cap * y.n_words) != cudaSuccess || dalloc(&y.d_obs, (size_t)y.cap) != cudaSuccess ||
+            dalloc(&y.d_flags, (size_t)y.cap) != cudaSuccess || dalloc(&y.d_iters, (size_t)y.cap) != cudaSuccess ||
+            cudaMallocHost(reinterpret_cast<void**>(&y.h_synd), (size_t)y.cap * y.n_words * 4) != cudaSuccess ||
+            cudaMallocHost(reinterpret_cast<void**>(&y.h_out), (size_t)y.cap * 2) != cudaSuccess)
+            return bad(fail(BP4M_ENOMEM, "out of memory for the fused decode's buffers"));
+        host[k].tb = dev_tables(g, y.type);
+        host[k].synd = y.d_synd;
+        host[k].obs_pred = y.d_obs;
+        host[k].flags = y.d_flags;
+        host[k].iters = y.d_iters;
+        m->total_cap += y.cap;
+        if (!g->prepared[m->pio]) {
+            if (prepare_decode_kernels(m->pio) != cudaSuccess) return bad(fail(BP4M_ECUDA, "kernel set-up failed"));
+            g->prepared[m->pio] = true;
+        }
+    }
+    if (dalloc(&m->d_entries, (size_t)n) != cudaSuccess || dalloc(&m->lists, (size_t)m->total_cap * kTiers) != cudaSuccess ||
+        dalloc(&m->small, 2 * kTiers + 1) != cudaSuccess || dalloc(&m->ctr, C_NUM) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&m->h_ctr), C_NUM * sizeof(unsigned long long)) != cudaSuccess)
+        return bad(fail(BP4M_ENOMEM, "out of memory for the fused decode's lists"));
+    if (cudaMemcpy(m->d_entries, host.data(), sizeof(MultiEntry) * n, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bad(fail(BP4M_ECUDA, "upload of the entries failed"));
+    // streaming tier: one slot per resident block, sized for max_defects
+    m->gslot_bytes = global_slot_bytes(1, max_defects, &m->gsmax);
+    m->gslots = (int)std::min<int64_t>(m->total_cap, (int64_t)m->num_sms * global_blocks_per_sm(1, max_defects));
+    if (cudaMalloc(&m->gscratch, m->gslot_bytes * m->gslots) != cudaSuccess)
+        return bad(fail(BP4M_ENOMEM, "out of memory for the streaming tier's scratch"));
+    if (cudaStreamCreateWithFlags(&m->st, cudaStreamNonBlocking) != cudaSuccess)
+        return bad(fail(BP4M_ECUDA, "cudaStreamCreate failed"));
+    return m;
+}
+
+int bp4m_multi_run(bp4m_multi* m, const uint32_t* const* syndromes, const int64_t* shots, uint8_t* const* obs_pred,
+                   uint8_t* const* converged) {
+    if (!m || !syndromes || !shots || !obs_pred) return fail(BP4M_EINVAL, "null argument");
+    const int n = (int)m->e.size();
+    std::vector<int64_t> sh(shots, shots + n);
+    for (int k = 0; k < n; ++k) {
+        if (sh[k] < 0 || sh[k] > m->e[k].cap) return fail(BP4M_EINVAL, "shots exceed the entry's capacity");
+        if (sh[k] > 0 && (!syndromes[k] || !obs_pred[k])) return fail(BP4M_EINVAL, "null buffer");
+        if (sh[k] > 0) std::memcpy(m->e[k].h_synd, syndromes[k], (size_t)sh[k] * m->e[k].n_words * 4);
+    }
+    if (cudaSetDevice(m->device) != cudaSuccess) return fail(BP4M_ECUDA, "cudaSetDevice failed");
+    if (!m->tuned) {
+        // autotuner: time every candidate tier plan on this run's shots, keep the fastest
+        cudaEvent_t e0, e1;
+        CK(cudaEventCreate(&e0));
+        CK(cudaEventCreate(&e1));
+        for (int pl = 0; pl < kPlanCount; ++pl) {
+            int rc = multi_enqueue(m, sh, pl);  // warm (first use of the plan's kernels)
+            if (rc) return rc;
+            CK(cudaEventRecord(e0, m->st));
+            rc = multi_enqueue(m, sh, pl);
+            if (rc) return rc;
+            CK(cudaEventRecord(e1, m->st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            m->plan_ms[pl] = ms;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        m->plan = (int)(std::min_element(m->plan_ms, m->plan_ms + kPlanCount) - m->plan_ms);
+        m->tuned = true;
+    } else if (m->use_graph) {
+        if (!m->exec || m->graph_shots != sh) {
+            if (m->exec) cudaGraphExecDestroy(m->exec);
+            m->exec = nullptr;
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(m->st, cudaStreamCaptureModeThreadLocal));
+            const int rc = multi_enqueue(m, sh, m->plan);
+            const cudaError_t ce = cudaStreamEndCapture(m->st, &graph);
+            if (rc) return rc;
+            CK(ce);
+            const cudaError_t ie = cudaGraphInstantiate(&m->exec, graph, 0);
+            cudaGraphDestroy(graph);
+            CK(ie);
+            m->graph_shots = sh;
+        }
+        CK(cudaGraphLaunch(m->exec, m->st));
+        ++m->replays;
+    } else {
+        const int rc = multi_enqueue(m, sh, m->plan);
+        if (rc) return rc;
+    }
+    CK(cudaStreamSynchronize(m->st));
+    ++m->runs;
+    for (int k = 0; k < n; ++k) {
+        if (sh[k] <= 0) continue;
+        const MultiHostEntry& x = m->e[k];
+        std::memcpy(obs_pred[k], x.h_out, (size_t)sh[k]);
+        if (converged && converged[k])
+            for (int64_t j = 0; j < sh[k]; ++j) converged[k][j] = (uint8_t)(x.h_out[x.cap + j] & F_CONVERGED);
+    }
+    if (m->h_ctr[C_ERRORS])
+        return fail(BP4M_EUNSUPPORTED, std::to_string(m->h_ctr[C_ERRORS]) + " shots exceed max_defects unsatisfied detectors");
+    return BP4M_OK;
+}
+
+int bp4m_multi_info(const bp4m_multi* m, bp4m_multi_info_t* out) {
+    if (!m || !out) return fail(BP4M_EINVAL, "null argument");
+    out->plan = m->plan;
+    for (int k = 0; k < 3; ++k) out->plan_ms[k] = m->plan_ms[k];
+    out->runs = m->runs;
+    out->graph_replays = m->replays;
+    out->msg_updates = m->h_ctr ? m->h_ctr[C_MSGS] : 0;
+    return BP4M_OK;
+}
+
+void bp4m_multi_destroy(bp4m_multi* m) {
+    if (m) multi_free(m);
 }
 
 const char* bp4m_last_error(void) { return g_last_error.c_str(); }

@@ -323,8 +323,6 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
     const int k0 = PAIR ? 2 * g : g;       // first column of this thread
     const bool own_diag = owner_of<PAIR, G>(i) == g;   // this thread holds column k = i of its row
     const int c_diag = reg_of<PAIR, G>(i);
-    const int n = a.tb.n_det;
-    const T* __restrict__ Ltab = Num<T>::L(a.tb);
     const int count = *a.count;
     const T ainv = (T)(1.0 / a.alpha);
     const bool full = (a.decoder == 1) || !a.early_exit;
@@ -354,9 +352,12 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
         __syncthreads();
         const int item = sh_item;
         if (item >= count) break;
-        const int64_t shot = a.list[item];
+        const ItemCtx ic = resolve_item(a, a.list[item]);
+        const int64_t shot = ic.shot;
+        const int n = ic.tb.n_det;
+        const T* __restrict__ Ltab = Num<T>::L(ic.tb);
         if (warp == 0) {
-            const int s0 = compact_defects(a.synd + (size_t)shot * a.tb.n_words, a.tb.n_words,
+            const int s0 = compact_defects(ic.synd + (size_t)shot * ic.tb.n_words, ic.tb.n_words,
                                            dets, SMAX, lane);
             if (lane == 0) sh_s = s0;
         }
@@ -373,9 +374,9 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
             if (tid == 0) {
                 const int its = full ? a.T : 1;
                 const int d0 = dets[0];
-                if (a.obs_pred) a.obs_pred[shot] = a.tb.P[(size_t)d0 * n + d0];
-                if (a.flags) a.flags[shot] = F_CONVERGED;
-                if (a.iters) a.iters[shot] = (int16_t)its;
+                if (ic.obs_pred) ic.obs_pred[shot] = ic.tb.P[(size_t)d0 * n + d0];
+                if (ic.flags) ic.flags[shot] = F_CONVERGED;
+                if (ic.iters) ic.iters[shot] = (int16_t)its;
                 if (tr_on && trl) trl[(size_t)shot * a.s_cap * a.s_cap] = Num<T>::pinf();
                 if (tr_on && a.tr_partner) {
                     a.tr_partner[(size_t)shot * a.s_cap] = 0;
@@ -493,9 +494,9 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
             // one defect: matched to the boundary along its reweighted path
             if (tid == 0) {
                 const int its = full ? a.T : 1;
-                if (a.obs_pred) a.obs_pred[shot] = Psh[0];
-                if (a.flags) a.flags[shot] = F_CONVERGED;
-                if (a.iters) a.iters[shot] = (int16_t)its;
+                if (ic.obs_pred) ic.obs_pred[shot] = Psh[0];
+                if (ic.flags) ic.flags[shot] = F_CONVERGED;
+                if (ic.iters) ic.iters[shot] = (int16_t)its;
                 acc_it += (unsigned long long)its;
                 acc_msg += (unsigned long long)its;
                 acc_def += 1;
@@ -731,8 +732,8 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                                 if (full) w = Wsh[i * SMAX + k];
                             } else {
                                 const size_t off = (size_t)dets[i] * n + dets[k];
-                                pc = a.tb.P[off];
-                                if (full) w = a.tb.W64[off];
+                                pc = ic.tb.P[off];
+                                if (full) w = ic.tb.W64[off];
                             }
                         }
                         rowacc[i] = w;
@@ -935,11 +936,11 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
             for (int k = s + tid; k < a.s_cap; k += NT) a.tr_partner[(size_t)shot * a.s_cap + k] = -1;
         }
         if (tid == 0) {
-            if (a.obs_pred) a.obs_pred[shot] = (uint8_t)out_par;
-            if (a.flags)
-                a.flags[shot] = (uint8_t)((any_conv ? F_CONVERGED : 0) | (forced_ran ? F_FORCED_RAN : 0) |
+            if (ic.obs_pred) ic.obs_pred[shot] = (uint8_t)out_par;
+            if (ic.flags)
+                ic.flags[shot] = (uint8_t)((any_conv ? F_CONVERGED : 0) | (forced_ran ? F_FORCED_RAN : 0) |
                                           (out_forced ? F_FROM_FORCED : 0));
-            if (a.iters) a.iters[shot] = (int16_t)t;
+            if (ic.iters) ic.iters[shot] = (int16_t)t;
             acc_it += (unsigned long long)t;
             acc_msg += (unsigned long long)s * s * t;
             acc_def += (unsigned long long)s;

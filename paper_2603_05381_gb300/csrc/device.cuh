@@ -16,6 +16,28 @@ struct DevTables {
     const uint8_t* P = nullptr;   // observable parity of the path
 };
 
+// One graph (and Pauli type) of a fused multi-graph launch: its tables, its syndromes and
+// its output arrays.  List items of such a launch are entry << kMultiShift | shot.
+struct MultiEntry {
+    DevTables tb;
+    const uint32_t* synd = nullptr;  // [shots][n_words]
+    uint8_t* obs_pred = nullptr;
+    uint8_t* flags = nullptr;
+    int16_t* iters = nullptr;
+};
+constexpr int kMultiShift = 21;  // shots per entry < 2^21, entries < 2^10
+constexpr int64_t kMultiMask = ((int64_t)1 << kMultiShift) - 1;
+
+// The graph, syndrome row and outputs of one decode item.
+struct ItemCtx {
+    DevTables tb;
+    const uint32_t* synd;
+    uint8_t* obs_pred;
+    uint8_t* flags;
+    int16_t* iters;
+    int64_t shot;
+};
+
 // Counter slots (unsigned long long) in the device counter block.
 enum CounterSlot {
     C_SHOTS = 0,
@@ -83,12 +105,37 @@ struct DecodeArgs {
     const uint32_t* rw_adj = nullptr;
     int rw_units = 0;
     int64_t rw_slot_bytes = 0;
+    // fused multi-graph launch: per-entry tables and buffers (tb / synd / outputs unused)
+    const MultiEntry* multi = nullptr;
     // global tier: scratch slots
     void* gscratch = nullptr;
     int64_t gscratch_bytes = 0;      // size of gscratch (checked by the reweighting launches)
     int64_t gslot_elems = 0;         // elements per slot for each of the three matrices
     int gsmax = 0;                   // largest s a slot holds
 };
+
+#ifdef __CUDACC__
+__device__ __forceinline__ ItemCtx resolve_item(const DecodeArgs& a, int64_t code) {
+    ItemCtx c;
+    if (a.multi) {
+        const MultiEntry& e = a.multi[code >> kMultiShift];
+        c.tb = e.tb;
+        c.synd = e.synd;
+        c.obs_pred = e.obs_pred;
+        c.flags = e.flags;
+        c.iters = e.iters;
+        c.shot = code & kMultiMask;
+    } else {
+        c.tb = a.tb;
+        c.synd = a.synd;
+        c.obs_pred = a.obs_pred;
+        c.flags = a.flags;
+        c.iters = a.iters;
+        c.shot = code;
+    }
+    return c;
+}
+#endif
 
 struct SampleArgs {
     uint64_t first_shot = 0;
@@ -141,7 +188,8 @@ cudaError_t launch_classify(const uint32_t* synd, int64_t shots, int n_words,
                             const TierPlan& plan, int32_t* lists /*[kTiers][shots]*/,
                             int32_t* counts, int32_t* max_s, uint8_t* obs_pred, uint8_t* flags,
                             int16_t* iters, int32_t* tr_defects, const uint8_t* skip,
-                            const uint8_t* skip_obs, const int16_t* skip_iters, cudaStream_t st);
+                            const uint8_t* skip_obs, const int16_t* skip_iters, cudaStream_t st,
+                            int64_t list_stride = 0 /* 0: shots */, int32_t item_base = 0);
 
 // 16-bit message storage (precision 2 = IEEE half, 3 = bfloat16) of the shared-memory tiers.
 cudaError_t launch_decode_tier_half(int precision, int tier, const DecodeArgs& a, int num_sms, cudaStream_t st,

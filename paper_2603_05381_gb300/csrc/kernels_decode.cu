@@ -357,8 +357,6 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
     T* Mo = slot + 3 * mat;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n = a.tb.n_det;
-    const T* __restrict__ Ltab = Num<T>::L(a.tb);
     const int64_t count = a.count ? (int64_t)*a.count : a.count_val;
     const T ainv = (T)(1.0 / a.alpha);
     const bool full = (a.decoder == 1) || !a.early_exit;
@@ -371,9 +369,12 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
         __syncthreads();
         const int item = sh_item;
         if (item >= count) break;
-        const int64_t shot = a.list ? (int64_t)a.list[item] : (int64_t)item;
+        const ItemCtx ic = resolve_item(a, a.list ? (int64_t)a.list[item] : (int64_t)item);
+        const int64_t shot = ic.shot;
+        const int n = ic.tb.n_det;
+        const T* __restrict__ Ltab = Num<T>::L(ic.tb);
         if (warp == 0) {
-            const int s0 = compact_defects(a.synd + (size_t)shot * a.tb.n_words, a.tb.n_words, dets, LD, lane);
+            const int s0 = compact_defects(ic.synd + (size_t)shot * ic.tb.n_words, ic.tb.n_words, dets, LD, lane);
             if (lane == 0) sh_s = s0;
         }
         __syncthreads();
@@ -498,8 +499,8 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
                         double w = 0.0;
                         if (k >= r) {
                             const size_t off = (size_t)dets[r] * n + dets[k];
-                            pc ^= a.tb.P[off];
-                            if (full) w = a.tb.W64[off];
+                            pc ^= ic.tb.P[off];
+                            if (full) w = ic.tb.W64[off];
                         }
                         rowacc[r] = w;
                     }
@@ -622,11 +623,11 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
             }
         }
         if (tid == 0) {
-            if (a.obs_pred) a.obs_pred[shot] = (uint8_t)out_par;
-            if (a.flags)
-                a.flags[shot] = (uint8_t)((any_conv ? F_CONVERGED : 0) | (forced_ran ? F_FORCED_RAN : 0) |
+            if (ic.obs_pred) ic.obs_pred[shot] = (uint8_t)out_par;
+            if (ic.flags)
+                ic.flags[shot] = (uint8_t)((any_conv ? F_CONVERGED : 0) | (forced_ran ? F_FORCED_RAN : 0) |
                                           (out_forced ? F_FROM_FORCED : 0));
-            if (a.iters) a.iters[shot] = (int16_t)t;
+            if (ic.iters) ic.iters[shot] = (int16_t)t;
             acc_it += (unsigned long long)t;
             acc_msg += (unsigned long long)s * s * t;
             acc_def += (unsigned long long)s;
@@ -783,17 +784,28 @@ cudaError_t run_stream(const DecodeArgs& a, int slots, cudaStream_t st) {
 
 // Columns per lane of the streaming kernel for the largest defect count of a batch; 0 when
 // the general global kernel takes the batch.
+// FP32 steps of 64 columns up to 448 keep the padding of a 160..450-defect shot below 1.3x
+// in each dimension.
 int stream_ch(int precision, int max_s) {
+    if (precision != 0) {
+        if (max_s <= 192) return 6;
+        if (max_s <= 256) return 8;
+        if (max_s <= 320) return 10;
+        if (max_s <= 384) return 12;
+        if (max_s <= 448) return 14;
+        if (max_s <= 512) return 16;
+        if (max_s <= 1024) return 32;
+        return 0;
+    }
     if (max_s <= 256) return 8;
     if (max_s <= 512) return 16;
-    if (precision != 0 && max_s <= 1024) return 32;
     return 0;
 }
 
 }  // namespace
 
 int global_blocks_per_sm(int precision, int max_s) {
-    return (precision != 0 && stream_ch(precision, max_s) == 8) ? kStreamBlocks<float, 8> : 1;
+    return (precision != 0 && stream_ch(precision, max_s) <= 8) ? kStreamBlocks<float, 8> : 1;
 }
 
 size_t global_slot_bytes(int precision, int max_s, int* gsmax_out) {
@@ -817,9 +829,15 @@ cudaError_t launch_decode_global(int precision, const DecodeArgs& a, int slots, 
             if (ch == 8) return run_stream<double, 8>(a, slots, st);
             return run_stream<double, 16>(a, slots, st);
         }
-        if (ch == 8) return run_stream<float, 8>(a, slots, st);
-        if (ch == 16) return run_stream<float, 16>(a, slots, st);
-        return run_stream<float, 32>(a, slots, st);
+        switch (ch) {
+            case 6: return run_stream<float, 6>(a, slots, st);
+            case 8: return run_stream<float, 8>(a, slots, st);
+            case 10: return run_stream<float, 10>(a, slots, st);
+            case 12: return run_stream<float, 12>(a, slots, st);
+            case 14: return run_stream<float, 14>(a, slots, st);
+            case 16: return run_stream<float, 16>(a, slots, st);
+            default: return run_stream<float, 32>(a, slots, st);
+        }
     }
     const size_t smem = (size_t)a.gsmax * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 16;
     cudaError_t e;

@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(kClsThreads) classify_kernel(
     const uint32_t* __restrict__ synd, int64_t shots, int n_words, TierPlan plan,
     int32_t* lists, int32_t* counts, int32_t* max_s, uint8_t* obs_pred, uint8_t* flags,
     int16_t* iters, int32_t* tr_defects, const uint8_t* skip, const uint8_t* skip_obs,
-    const int16_t* skip_iters) {
+    const int16_t* skip_iters, int64_t list_stride, int32_t item_base) {
     int local_max = 0;
     for (int64_t shot = (int64_t)blockIdx.x * kClsThreads + threadIdx.x; shot < shots;
          shot += (int64_t)gridDim.x * kClsThreads) {
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kClsThreads) classify_kernel(
                 break;
             }
         const int pos = atomicAdd(counts + tier, 1);
-        lists[(size_t)tier * shots + pos] = (int32_t)shot;
+        lists[(size_t)tier * list_stride + pos] = item_base | (int32_t)shot;
     }
 #pragma unroll
     for (int off = 16; off; off >>= 1) local_max = max(local_max, __shfl_xor_sync(0xffffffffu, local_max, off));
@@ -232,11 +232,12 @@ cudaError_t launch_sample_code_capacity(const SampleArgs& a, cudaStream_t st) {
 cudaError_t launch_classify(const uint32_t* synd, int64_t shots, int n_words, const TierPlan& plan,
                             int32_t* lists, int32_t* counts, int32_t* max_s, uint8_t* obs_pred,
                             uint8_t* flags, int16_t* iters, int32_t* tr_defects, const uint8_t* skip,
-                            const uint8_t* skip_obs, const int16_t* skip_iters, cudaStream_t st) {
+                            const uint8_t* skip_obs, const int16_t* skip_iters, cudaStream_t st,
+                            int64_t list_stride, int32_t item_base) {
     if (shots <= 0) return cudaSuccess;
     classify_kernel<<<grid_for(shots, kClsThreads, 152 * 8), kClsThreads, 0, st>>>(
         synd, shots, n_words, plan, lists, counts, max_s, obs_pred, flags, iters, tr_defects, skip,
-        skip_obs, skip_iters);
+        skip_obs, skip_iters, list_stride > 0 ? list_stride : shots, item_base);
     return cudaGetLastError();
 }
 
