@@ -410,9 +410,14 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
         bool any_conv = false, forced_ran = false;
         int out_par = 0, out_forced = 0, out_from_best = 0;
 
+        // BP4M with early exit: the decisions of lambda^t are taken inside the update pass that
+        // reads the same rows (Lg, Mc, Mo once per iteration instead of twice); only the last
+        // iteration, which may need forced convergence, keeps the separate decision pass
+        const bool merged = !TRACE && a.decoder == 0 && a.early_exit;
         for (;;) {
             const T* Mc = Mtb[cur];
-            if (t > 0) {
+            const bool fuse = merged && t > 0 && t < a.T;
+            if (t > 0 && !fuse) {
                 // ---- decisions of lambda^t = l + (M[r][k] + M[k][r])
                 int ok_all = 1;
                 for (int r = warp; r < s; r += kStreamWarps) {
@@ -550,6 +555,7 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
             // ---- update pass: M' for every row, batch by batch
             T* Mn = Mtb[cur ^ 1];
             const int nbatch = (s + kStreamWarps - 1) / kStreamWarps;
+            int ok_w = 1;  // fused decisions: every row of this warp keeps exactly one variable
             for (int b = 0; b < nbatch; ++b) {
                 const int r = b * kStreamWarps + warp;
                 T* srow = stage + warp * SP;
@@ -557,6 +563,19 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
                     const T* lrow = Lg + (size_t)r * LD;
                     const T* xrow = Mc + (size_t)r * LD;
                     T* orow = Mo + (size_t)r * LD;
+                    if (fuse) {
+                        int cnt = 0, chosen = 0x7fffffff;
+#pragma unroll
+                        for (int c = 0; c < CH; ++c) {
+                            const int k = lane + 32 * c;
+                            const T lam = lrow[k] + (orow[k] + xrow[k]);
+                            const unsigned bal = __ballot_sync(kFull, lam > T(0));
+                            cnt += __popc(bal);
+                            if (bal && chosen == 0x7fffffff) chosen = 32 * c + __ffs(bal) - 1;
+                        }
+                        if (lane == 0) choice[r] = chosen;
+                        ok_w &= (cnt == 1);
+                    }
                     T q[CH];
                     T m1 = ninf, m2 = ninf;
                     int am = 0x7fffffff;
@@ -611,6 +630,18 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
                     if (w < rows) Mn[(size_t)k * LD + r0 + w] = stage[w * SP + k];
                 }
                 __syncthreads();
+            }
+            if (fuse && __syncthreads_and(ok_w)) {
+                // lambda^t converged: its matching is the output (the update just made is unused)
+                any_conv = true;
+                int pc = 0;
+                for (int r = tid; r < s; r += kStreamThreads) {
+                    const int k = choice[r];
+                    if (k >= r) pc ^= ic.tb.P[(size_t)dets[r] * n + dets[k]];
+                }
+                out_par = __syncthreads_count(pc) & 1;
+                out_forced = 0;
+                break;
             }
             cur ^= 1;
             ++t;

@@ -215,6 +215,8 @@ def test_every_tier_boundary_d13(torch, prec, early):
     assert all(m < tau for _, m in bad), bad
     assert res["obs"][0] == 0 and res["iters"][0] == 0 and res["flags"][0] & 1
     assert res["iters"][1] == (1 if early else T) and res["partner"][1][0] == 0
+    # the production kernels (no trace) agree with the traced ones shot for shot
+    assert np.array_equal(res["obs"], res["obs2"]) and np.array_equal(res["flags"] & 1, res["conv"])
 
 
 def test_host_buffers_match_device_buffers(torch):
