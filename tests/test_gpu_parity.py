@@ -266,6 +266,62 @@ def test_bench_workload_d13_sampled_shots(torch):
     assert counts["iterations"] == int(its.cpu().numpy().astype(np.int64).sum())
 
 
+def test_code_capacity_sweep_largest_point_sampled_shots(torch):
+    # the largest point of the code-capacity sweep: rotated d = 21, p = 0.20, 2^20 shots in
+    # one batched launch, FP32, iterations capped at 2d; sampled shots of both types against
+    # the oracle, and the fused sample-and-decode counts against the per-shot outputs
+    d, p, n = 21, 0.20, 1 << 20
+    T = 2 * d
+    g = pkg.Graph(d, "code_capacity", p)
+    synds, obs = gpu_sample(g, 0, n, seed=3)
+    code = rotated_code(d)
+    rng = np.random.default_rng(8)
+    rows = np.sort(rng.choice(n, size=12, replace=False))
+    fails = []
+    for ty, kind in ((0, "X"), (1, "Z")):
+        opts = pkg.make_opts(precision="fp32", type=ty)
+        pred = torch.empty((n,), dtype=torch.uint8, device="cuda")
+        conv = torch.empty((n,), dtype=torch.uint8, device="cuda")
+        its = torch.empty((n,), dtype=torch.int16, device="cuda")
+        g.decode_batch(synds[ty], T, opts, pred, conv, its)
+        torch.cuda.synchronize()
+        tb = code_capacity_tables(code_capacity_graph(code, kind), p)
+        sub = synds[ty][torch.as_tensor(rows, device="cuda")].contiguous()
+        res = gpu_decode(g, sub, T, opts, s_cap=160)
+        assert np.array_equal(res["obs"], pred.cpu().numpy()[rows])
+        cnt, bad = compare_shots(tb, as_bool(sub, tb.n_det), res, T, range(len(rows)), TAU32)
+        print("d21 p0.20 %s: %d/%d sampled shots differ %s" % (kind, len(bad), cnt, bad))
+        assert all(m < TAU32 for _, m in bad), bad
+        fails.append(pred.cpu().numpy() != obs[ty].cpu().numpy())
+    counts = g.sample_and_decode(n, seed=3, iters=T, opts=pkg.make_opts(precision="fp32"))
+    assert counts["fail"][0] == int(fails[0].sum()) and counts["fail"][1] == int(fails[1].sum())
+    assert counts["fail"][2] == int((fails[0] | fails[1]).sum())
+
+
+def test_circuit_largest_point_sampled_shots(torch):
+    # the largest circuit-level point: d = 15, p = 0.010 (some 300 unsatisfied detectors a
+    # shot: the streaming tier), 2^18 shots, FP32, T = 50 with early exit
+    g, og, ot = circuit_pair(15, 0.010)
+    n, T = 1 << 18, 50
+    (synd,), obs = gpu_sample(g, 0, n, seed=2)
+    opts = pkg.make_opts(precision="fp32", early_exit=True)
+    pred = torch.empty((n,), dtype=torch.uint8, device="cuda")
+    conv = torch.empty((n,), dtype=torch.uint8, device="cuda")
+    its = torch.empty((n,), dtype=torch.int16, device="cuda")
+    g.decode_batch(synd, T, opts, pred, conv, its)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(6)
+    rows = np.sort(rng.choice(n, size=5, replace=False))
+    sub = synd[torch.as_tensor(rows, device="cuda")].contiguous()
+    res = gpu_decode(g, sub, T, opts, s_cap=600)
+    assert np.array_equal(res["obs"], pred.cpu().numpy()[rows]) and np.array_equal(res["iters"], its.cpu().numpy()[rows])
+    sb = as_bool(sub, og.n_det)
+    print("d15 p0.010 sampled defect counts", sb.sum(axis=1))
+    cnt, bad = compare_shots(ot, sb, res, T, range(len(rows)), TAU32)
+    print("d15 p0.010: %d/%d sampled shots differ %s" % (len(bad), cnt, bad))
+    assert all(m < TAU32 for _, m in bad), bad
+
+
 # ------------------------------------------------------------------ unrotated code
 
 
