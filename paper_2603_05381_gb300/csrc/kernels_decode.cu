@@ -321,6 +321,10 @@ constexpr int kStreamThreads = kStreamWarps * 32;
 // block's L2 latency overlaps the other's arithmetic.
 template <typename T, int CH>
 constexpr int kStreamBlocks = (sizeof(T) == 4 && CH <= 8) ? 2 : 1;
+// Warps per block: the FP32 320..512-column variants run one 32-warp block per SM (twice the
+// rows in flight per batch and half the batch barriers of 16 warps), the others 16.
+template <typename T, int CH>
+constexpr int kStreamWarpsOf = (sizeof(T) == 4 && CH >= 10 && CH <= 16) ? 32 : kStreamWarps;
 
 template <typename T>
 __device__ __forceinline__ T warp_max(T v) {
@@ -336,13 +340,14 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-template <typename T, int CH, bool TRACE>
-__global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_stream_kernel(const DecodeArgs a) {
+template <typename T, int CH, bool TRACE, int W>
+__global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, CH> : 1) decode_stream_kernel(const DecodeArgs a) {
+    constexpr int NTH = W * 32;
     constexpr int LD = 32 * CH;
     constexpr int SP = LD + 1;  // stage pitch: odd, so the transposed read is conflict-free
     extern __shared__ __align__(16) unsigned char smem[];
-    T* stage = reinterpret_cast<T*>(smem);                          // [kStreamWarps][SP]
-    double* rowacc = reinterpret_cast<double*>(stage + kStreamWarps * SP + ((kStreamWarps * SP) & 1));
+    T* stage = reinterpret_cast<T*>(smem);                          // [W][SP]
+    double* rowacc = reinterpret_cast<double*>(stage + W * SP + ((W * SP) & 1));
     int* dets = reinterpret_cast<int*>(rowacc + LD);
     int* choice = dets + LD;
     short* bestp = reinterpret_cast<short*>(choice + LD);
@@ -384,7 +389,7 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
             continue;
         }
         const bool tr_on = TRACE && s <= a.s_cap;
-        for (int r = warp; r < s; r += kStreamWarps) {
+        for (int r = warp; r < s; r += W) {
             const T* trow = Ltab + (size_t)dets[r] * n;
             for (int k = lane; k < LD; k += 32) {
                 Lg[(size_t)r * LD + k] = k < s ? (T)(__ldg(trow + dets[k]) * (T)kLog2e) : ninf;
@@ -393,7 +398,7 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
                 Mo[(size_t)r * LD + k] = T(0);
             }
         }
-        for (int r = tid; r < LD; r += kStreamThreads) {
+        for (int r = tid; r < LD; r += NTH) {
             matched[r] = r >= s;
             bestp[r] = -1;
         }
@@ -420,7 +425,7 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
             if (t > 0 && !fuse) {
                 // ---- decisions of lambda^t = l + (M[r][k] + M[k][r])
                 int ok_all = 1;
-                for (int r = warp; r < s; r += kStreamWarps) {
+                for (int r = warp; r < s; r += W) {
                     const T* lrow = Lg + (size_t)r * LD;
                     const T* xrow = Mc + (size_t)r * LD;
                     const T* orow = Mo + (size_t)r * LD;
@@ -446,10 +451,10 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
                 } else if (a.decoder == 1 || t == a.T) {
                     // ---- forced convergence on lambda^t by locally dominant rounds
                     forced_ran = true;
-                    for (int r = tid; r < s; r += kStreamThreads) matched[r] = 0;
+                    for (int r = tid; r < s; r += NTH) matched[r] = 0;
                     __syncthreads();
                     for (int round = 0; round < s; ++round) {
-                        for (int r = warp; r < s; r += kStreamWarps) {
+                        for (int r = warp; r < s; r += W) {
                             if (matched[r]) continue;  // uniform per warp
                             const T* lrow = Lg + (size_t)r * LD;
                             const T* xrow = Mc + (size_t)r * LD;
@@ -480,7 +485,7 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
                         }
                         __syncthreads();
                         int left = 0;
-                        for (int r = tid; r < s; r += kStreamThreads) {
+                        for (int r = tid; r < s; r += NTH) {
                             if (matched[r]) continue;
                             const int pk = choice[r];
                             const bool newm = (pk == r) || (choice[pk] == r);
@@ -488,7 +493,7 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
                             left += !newm;
                         }
                         __syncthreads();
-                        for (int r = tid; r < s; r += kStreamThreads)
+                        for (int r = tid; r < s; r += NTH)
                             if (!matched[r] && rowacc[r] != 0.0) matched[r] = 1;
                         if (tid == 0) acc_fcr += 1;
                         if (__syncthreads_count(left) == 0) break;
@@ -499,7 +504,7 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
                 }
                 if (have_cand) {
                     int pc = 0;
-                    for (int r = tid; r < s; r += kStreamThreads) {
+                    for (int r = tid; r < s; r += NTH) {
                         const int k = choice[r];
                         double w = 0.0;
                         if (k >= r) {
@@ -534,7 +539,7 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
                         }
                         __syncthreads();
                         if (sh_improve)
-                            for (int r = tid; r < s; r += kStreamThreads) bestp[r] = (short)choice[r];
+                            for (int r = tid; r < s; r += NTH) bestp[r] = (short)choice[r];
                         if (t == a.T || (a.decoder == 0 && cand_forced)) {
                             finish = true;
                             if (a.decoder == 0 && cand_forced && !sh_use_best) {
@@ -554,10 +559,10 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
             }
             // ---- update pass: M' for every row, batch by batch
             T* Mn = Mtb[cur ^ 1];
-            const int nbatch = (s + kStreamWarps - 1) / kStreamWarps;
+            const int nbatch = (s + W - 1) / W;
             int ok_w = 1;  // fused decisions: every row of this warp keeps exactly one variable
             for (int b = 0; b < nbatch; ++b) {
-                const int r = b * kStreamWarps + warp;
+                const int r = b * W + warp;
                 T* srow = stage + warp * SP;
                 if (r < s) {
                     const T* lrow = Lg + (size_t)r * LD;
@@ -623,10 +628,10 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
                 }
                 __syncthreads();
                 // transposed write of the batch: Mn[k][b*W + w] = stage[w][k]
-                const int r0 = b * kStreamWarps;
-                const int rows = min(kStreamWarps, s - r0);
-                for (int e = tid; e < s * kStreamWarps; e += kStreamThreads) {
-                    const int k = e / kStreamWarps, w = e % kStreamWarps;
+                const int r0 = b * W;
+                const int rows = min(W, s - r0);
+                for (int e = tid; e < s * W; e += NTH) {
+                    const int k = e / W, w = e % W;
                     if (w < rows) Mn[(size_t)k * LD + r0 + w] = stage[w * SP + k];
                 }
                 __syncthreads();
@@ -635,7 +640,7 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
                 // lambda^t converged: its matching is the output (the update just made is unused)
                 any_conv = true;
                 int pc = 0;
-                for (int r = tid; r < s; r += kStreamThreads) {
+                for (int r = tid; r < s; r += NTH) {
                     const int k = choice[r];
                     if (k >= r) pc ^= ic.tb.P[(size_t)dets[r] * n + dets[k]];
                 }
@@ -647,7 +652,7 @@ __global__ void __launch_bounds__(kStreamThreads, kStreamBlocks<T, CH>) decode_s
             ++t;
         }
         if (tr_on && a.tr_partner) {
-            for (int r = tid; r < a.s_cap; r += kStreamThreads) {
+            for (int r = tid; r < a.s_cap; r += NTH) {
                 int pk = -1;
                 if (r < s) pk = out_from_best ? (int)bestp[r] : choice[r];
                 a.tr_partner[(size_t)shot * a.s_cap + r] = (int16_t)pk;
@@ -803,13 +808,14 @@ namespace {
 template <typename T, int CH>
 cudaError_t run_stream(const DecodeArgs& a, int slots, cudaStream_t st) {
     constexpr int LD = 32 * CH;
-    const size_t smem = (size_t)kStreamWarps * (LD + 1) * sizeof(T) + sizeof(T) +
+    constexpr int W = kStreamWarpsOf<T, CH>;
+    const size_t smem = (size_t)W * (LD + 1) * sizeof(T) + sizeof(T) +
                         (size_t)LD * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 16;
     const bool tr = a.tr_lambda != nullptr || a.tr_partner != nullptr;
-    auto kern = tr ? decode_stream_kernel<T, CH, true> : decode_stream_kernel<T, CH, false>;
+    auto kern = tr ? decode_stream_kernel<T, CH, true, W> : decode_stream_kernel<T, CH, false, W>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<slots, kStreamThreads, smem, st>>>(a);
+    kern<<<slots, W * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
