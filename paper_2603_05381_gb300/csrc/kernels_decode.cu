@@ -325,6 +325,24 @@ constexpr int kStreamBlocks = (sizeof(T) == 4 && CH <= 8) ? 2 : 1;
 // rows in flight per batch and half the batch barriers of 16 warps), the others 16.
 template <typename T, int CH>
 constexpr int kStreamWarpsOf = (sizeof(T) == 4 && CH >= 10 && CH <= 16) ? 32 : kStreamWarps;
+// Row prefetch of the update pass: each warp copies its next row of Lg, Mc and Mo into
+// shared memory (asynchronous copies) while it updates the current one.
+//   1: the row is moved into registers and the next copy issued at once (FP32, <= 256 columns)
+//   2: the row is read in place and the next copy issued after its last read (FP32, 320 and
+//      384 columns, where the register copy would spill and 3 x 32 rows still fit)
+//   0: rows are read from global memory
+template <typename T, int CH>
+constexpr int kStreamPrefetch = sizeof(T) != 4 ? 0 : CH <= 8 ? 1 : CH <= 12 ? 2 : 0;
+
+// 16-byte asynchronous global->shared copies (cp.async, L2 only), used to fetch a warp's next
+// factor row while it works on the current one
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    const size_t g = __cvta_generic_to_global(gmem_src);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 template <typename T>
 __device__ __forceinline__ T warp_max(T v) {
@@ -345,8 +363,13 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
     constexpr int NTH = W * 32;
     constexpr int LD = 32 * CH;
     constexpr int SP = LD + 1;  // stage pitch: odd, so the transposed read is conflict-free
+    // FP32 variants of up to 256 columns prefetch each warp's next row of Lg, Mc and Mo into
+    // shared memory (pf[W][3][LD]) during the current row's update
+    constexpr int PFM = kStreamPrefetch<T, CH>;
+    constexpr bool PF = PFM != 0;
     extern __shared__ __align__(16) unsigned char smem[];
-    T* stage = reinterpret_cast<T*>(smem);                          // [W][SP]
+    T* const pf = reinterpret_cast<T*>(smem);
+    T* stage = pf + (PF ? W * 3 * LD : 0);                          // [W][SP]
     double* rowacc = reinterpret_cast<double*>(stage + W * SP + ((W * SP) & 1));
     int* dets = reinterpret_cast<int*>(rowacc + LD);
     int* choice = dets + LD;
@@ -561,6 +584,19 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
             T* Mn = Mtb[cur ^ 1];
             const int nbatch = (s + W - 1) / W;
             int ok_w = 1;  // fused decisions: every row of this warp keeps exactly one variable
+            T* const pbuf = pf + warp * 3 * LD;
+            // row rr of Lg, Mc and Mo into this warp's prefetch buffer (one commit group)
+            auto prefetch = [&](int rr) {
+                const T* src[3] = {Lg + (size_t)rr * LD, Mc + (size_t)rr * LD, Mo + (size_t)rr * LD};
+                constexpr int V = LD * (int)sizeof(T) / 16;  // 16-byte chunks per row
+#pragma unroll
+                for (int m = 0; m < 3; ++m)
+                    for (int v = lane; v < V; v += 32) cp_async16(pbuf + m * LD + v * (16 / (int)sizeof(T)),
+                                                                  src[m] + v * (16 / (int)sizeof(T)));
+                cp_async_commit();
+            };
+            if constexpr (PF)
+                if (warp < s) prefetch(warp);
             for (int b = 0; b < nbatch; ++b) {
                 const int r = b * W + warp;
                 T* srow = stage + warp * SP;
@@ -568,12 +604,43 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                     const T* lrow = Lg + (size_t)r * LD;
                     const T* xrow = Mc + (size_t)r * LD;
                     T* orow = Mo + (size_t)r * LD;
+                    T lv[PFM == 1 ? CH : 1], xv[PFM == 1 ? CH : 1], ov[PFM == 1 ? CH : 1];
+                    if constexpr (PF) {
+                        cp_async_wait_all();
+                        __syncwarp();
+                    }
+                    if constexpr (PFM == 1) {
+#pragma unroll
+                        for (int c = 0; c < CH; ++c) {
+                            const int k = lane + 32 * c;
+                            lv[c] = pbuf[k];
+                            xv[c] = pbuf[LD + k];
+                            ov[c] = pbuf[2 * LD + k];
+                        }
+                        __syncwarp();
+                        if (r + W < s) prefetch(r + W);
+                    }
+                    // the row's prior, incoming message and own output at column lane + 32 c
+                    auto LV = [&](int c) -> T {
+                        if constexpr (PFM == 1) return lv[c];
+                        else if constexpr (PFM == 2) return pbuf[lane + 32 * c];
+                        else return lrow[lane + 32 * c];
+                    };
+                    auto XV = [&](int c) -> T {
+                        if constexpr (PFM == 1) return xv[c];
+                        else if constexpr (PFM == 2) return pbuf[LD + lane + 32 * c];
+                        else return xrow[lane + 32 * c];
+                    };
+                    auto OV = [&](int c) -> T {
+                        if constexpr (PFM == 1) return ov[c];
+                        else if constexpr (PFM == 2) return pbuf[2 * LD + lane + 32 * c];
+                        else return orow[lane + 32 * c];
+                    };
                     if (fuse) {
                         int cnt = 0, chosen = 0x7fffffff;
 #pragma unroll
                         for (int c = 0; c < CH; ++c) {
-                            const int k = lane + 32 * c;
-                            const T lam = lrow[k] + (orow[k] + xrow[k]);
+                            const T lam = LV(c) + (OV(c) + XV(c));
                             const unsigned bal = __ballot_sync(kFull, lam > T(0));
                             cnt += __popc(bal);
                             if (bal && chosen == 0x7fffffff) chosen = 32 * c + __ffs(bal) - 1;
@@ -587,12 +654,17 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
 #pragma unroll
                     for (int c = 0; c < CH; ++c) {
                         const int k = lane + 32 * c;
-                        const T v = B2<T>::fma_(xrow[k], ainv, lrow[k]);
+                        const T v = B2<T>::fma_(XV(c), ainv, LV(c));
                         q[c] = v;
                         const bool gt = v > m1;
                         m2 = B2<T>::mx(m2, B2<T>::mn(v, m1));
                         m1 = B2<T>::mx(m1, v);
                         am = gt ? k : am;
+                    }
+                    if constexpr (PFM == 2) {
+                        // the last read of this row's buffer: the next row may replace it
+                        __syncwarp();
+                        if (r + W < s) prefetch(r + W);
                     }
 #pragma unroll
                     for (int off = 16; off; off >>= 1) {
@@ -809,7 +881,8 @@ template <typename T, int CH>
 cudaError_t run_stream(const DecodeArgs& a, int slots, cudaStream_t st) {
     constexpr int LD = 32 * CH;
     constexpr int W = kStreamWarpsOf<T, CH>;
-    const size_t smem = (size_t)W * (LD + 1) * sizeof(T) + sizeof(T) +
+    const size_t smem = (kStreamPrefetch<T, CH> != 0 ? (size_t)W * 3 * LD * sizeof(T) : 0) +
+                        (size_t)W * (LD + 1) * sizeof(T) + sizeof(T) +
                         (size_t)LD * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 16;
     const bool tr = a.tr_lambda != nullptr || a.tr_partner != nullptr;
     auto kern = tr ? decode_stream_kernel<T, CH, true, W> : decode_stream_kernel<T, CH, false, W>;

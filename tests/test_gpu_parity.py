@@ -219,6 +219,37 @@ def test_every_tier_boundary_d13(torch, prec, early):
     assert np.array_equal(res["obs"], res["obs2"]) and np.array_equal(res["flags"] & 1, res["conv"])
 
 
+# the streaming tier's column count follows the batch's largest defect count: 192, 256, 320,
+# 384, 448, 512 or 1024 columns in FP32 (256 or 512 in FP64); every width once, with the
+# posteriors after exactly T iterations and the early-exit decisions against the oracle
+@pytest.mark.parametrize("prec,sizes", [
+    ("fp32", [40, 161, 192]), ("fp32", [193, 256]), ("fp32", [120, 257, 320]), ("fp32", [321, 384]),
+    ("fp32", [385, 448]), ("fp32", [449, 512]), ("fp32", [513, 600]), ("fp64", [113, 256]), ("fp64", [257, 512])])
+def test_streaming_tier_every_width(torch, prec, sizes):
+    g, og, ot = circuit_pair(13, 0.005)
+    sb = _random_syndromes(og.n_det, sizes, seed=sum(sizes))
+    synd = torch.as_tensor(pack_syndromes(sb).view(np.int32), device="cuda")
+    T = 3
+    cap = max(sizes)
+    res = gpu_decode(g, synd, T, pkg.make_opts(precision=prec, early_exit=False), s_cap=cap)
+    assert list(res["s"]) == sizes
+    rtol = 1e-10 if prec == "fp64" else 1e-4
+    worst = 0.0
+    for k, s in enumerate(sizes):
+        dets = np.flatnonzero(sb[k])
+        L = ot.L[np.ix_(dets, dets)]
+        lam = run_bp(L, T)[-1][1]
+        got = res["lam"][k][:s, :s].astype(np.float64)
+        worst = max(worst, float(np.max(np.abs(got - lam) / (np.abs(L) + 1.0))))
+    print("%s %s: worst |dlambda|/(|l|+1) = %.3g" % (prec, sizes, worst))
+    assert worst < rtol
+    res = gpu_decode(g, synd, T, pkg.make_opts(precision=prec, early_exit=True), s_cap=cap)
+    tau = TAU64 if prec == "fp64" else TAU32
+    cnt, bad = compare_shots(ot, sb, res, T, range(len(sizes)), tau)
+    assert all(m < tau for _, m in bad), bad
+    assert np.array_equal(res["obs"], res["obs2"]) and np.array_equal(res["flags"] & 1, res["conv"])
+
+
 def test_host_buffers_match_device_buffers(torch):
     g, og, ot = circuit_pair(5, 0.008)
     n, T = 2000, 20
