@@ -311,8 +311,8 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
 //   Mt[b][r][k]  incoming message M[k][r], double buffered (b = iteration parity)
 //   Mo[r][k]     the row's own outputs M[r][k], updated in place by the owning warp
 // The diagonal of Mt is kept 0, so Q_rr = l_rr and lambda_rr = l_rr + Mo[r][r].  Outputs go
-// to Mt[next][k][r]; a batch of kStreamWarps consecutive rows stages them in shared memory
-// and writes kStreamWarps consecutive floats per column k.  Iteration = decision pass
+// to Mt[next][k][r]; a batch of W consecutive rows (one per warp) stages them in shared
+// memory and writes W consecutive elements per column k.  Iteration = decision pass
 // (lambda of the previous update, convergence vote, candidates / forced convergence), then
 // the update pass.
 constexpr int kStreamWarps = 16;
@@ -321,18 +321,20 @@ constexpr int kStreamThreads = kStreamWarps * 32;
 // block's L2 latency overlaps the other's arithmetic.
 template <typename T, int CH>
 constexpr int kStreamBlocks = (sizeof(T) == 4 && CH <= 8) ? 2 : 1;
-// Warps per block: the FP32 320..512-column variants run one 32-warp block per SM (twice the
-// rows in flight per batch and half the batch barriers of 16 warps), the others 16.
+// Warps per block (one row in flight per warp, each with a 3-row prefetch buffer in shared
+// memory): FP32 320 and 384 columns run one 32-warp block per SM (twice the rows in flight
+// per batch and half the batch barriers of 16 warps), 896 and 1024 columns one 12-warp block
+// (the largest count whose prefetch buffers and output stage fit in 227 KB), the others 16.
 template <typename T, int CH>
-constexpr int kStreamWarpsOf = (sizeof(T) == 4 && CH >= 10 && CH <= 16) ? 32 : kStreamWarps;
+constexpr int kStreamWarpsOf = sizeof(T) != 4 ? kStreamWarps : (CH >= 10 && CH <= 12) ? 32 : CH >= 28 ? 12 : kStreamWarps;
 // Row prefetch of the update pass: each warp copies its next row of Lg, Mc and Mo into
 // shared memory (asynchronous copies) while it updates the current one.
 //   1: the row is moved into registers and the next copy issued at once (FP32, <= 256 columns)
-//   2: the row is read in place and the next copy issued after its last read (FP32, 320 and
-//      384 columns, where the register copy would spill and 3 x 32 rows still fit)
-//   0: rows are read from global memory
+//   2: the row is read in place and the next copy issued after its last read (FP32, 320 to
+//      1024 columns, where the register copy would spill)
+//   0: rows are read from global memory (FP64)
 template <typename T, int CH>
-constexpr int kStreamPrefetch = sizeof(T) != 4 ? 0 : CH <= 8 ? 1 : CH <= 12 ? 2 : 0;
+constexpr int kStreamPrefetch = sizeof(T) != 4 ? 0 : CH <= 8 ? 1 : 2;
 
 // 16-byte asynchronous global->shared copies (cp.async, L2 only), used to fetch a warp's next
 // factor row while it works on the current one
@@ -894,8 +896,9 @@ cudaError_t run_stream(const DecodeArgs& a, int slots, cudaStream_t st) {
 
 // Columns per lane of the streaming kernel for the largest defect count of a batch; 0 when
 // the general global kernel takes the batch.
-// FP32 steps of 64 columns up to 448 keep the padding of a 160..450-defect shot below 1.3x
-// in each dimension.
+// FP32 steps of 64 columns up to 512 and of 128 columns up to 1024 keep the padding of a
+// shot of more than 160 defects below 1.3x in each dimension (d = 15..25 circuits at
+// p = 0.005 average 194, 283, 395, 534, 702 and 902 defects).
 int stream_ch(int precision, int max_s) {
     if (precision != 0) {
         if (max_s <= 192) return 6;
@@ -904,6 +907,9 @@ int stream_ch(int precision, int max_s) {
         if (max_s <= 384) return 12;
         if (max_s <= 448) return 14;
         if (max_s <= 512) return 16;
+        if (max_s <= 640) return 20;
+        if (max_s <= 768) return 24;
+        if (max_s <= 896) return 28;
         if (max_s <= 1024) return 32;
         return 0;
     }
@@ -946,6 +952,9 @@ cudaError_t launch_decode_global(int precision, const DecodeArgs& a, int slots, 
             case 12: return run_stream<float, 12>(a, slots, st);
             case 14: return run_stream<float, 14>(a, slots, st);
             case 16: return run_stream<float, 16>(a, slots, st);
+            case 20: return run_stream<float, 20>(a, slots, st);
+            case 24: return run_stream<float, 24>(a, slots, st);
+            case 28: return run_stream<float, 28>(a, slots, st);
             default: return run_stream<float, 32>(a, slots, st);
         }
     }

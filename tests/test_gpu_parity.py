@@ -220,11 +220,13 @@ def test_every_tier_boundary_d13(torch, prec, early):
 
 
 # the streaming tier's column count follows the batch's largest defect count: 192, 256, 320,
-# 384, 448, 512 or 1024 columns in FP32 (256 or 512 in FP64); every width once, with the
-# posteriors after exactly T iterations and the early-exit decisions against the oracle
+# 384, 448, 512, 640, 768, 896 or 1024 columns in FP32 (256 or 512 in FP64); every width
+# once, with the posteriors after exactly T iterations and the early-exit decisions against
+# the oracle
 @pytest.mark.parametrize("prec,sizes", [
     ("fp32", [40, 161, 192]), ("fp32", [193, 256]), ("fp32", [120, 257, 320]), ("fp32", [321, 384]),
-    ("fp32", [385, 448]), ("fp32", [449, 512]), ("fp32", [513, 600]), ("fp64", [113, 256]), ("fp64", [257, 512])])
+    ("fp32", [385, 448]), ("fp32", [449, 512]), ("fp32", [513, 600]), ("fp32", [300, 700]), ("fp32", [200, 800]),
+    ("fp32", [100, 900]), ("fp64", [113, 256]), ("fp64", [257, 512])])
 def test_streaming_tier_every_width(torch, prec, sizes):
     g, og, ot = circuit_pair(13, 0.005)
     sb = _random_syndromes(og.n_det, sizes, seed=sum(sizes))
