@@ -503,10 +503,13 @@ int decode_device(bp4m_graph* g, Workspace& w, int ty, const uint32_t* synd, int
         const int max_s = w.host_small[2 * kTiers];
         int gsmax = 0;
         const size_t slot_bytes = global_slot_bytes(prec, max_s, &gsmax);
-        int slots = std::min(n_glob, g->num_sms * global_blocks_per_sm(prec, max_s));
+        // the scratch holds a slot for every resident block, whatever this batch's count, so
+        // that it is reallocated (a device-wide synchronisation) only for a wider slot
+        int full = g->num_sms * global_blocks_per_sm(prec, max_s);
         const size_t budget = (size_t)16 << 30;
-        while (slots > 1 && (size_t)slots * slot_bytes > budget) --slots;
-        int rc = ensure_gscratch(w, (size_t)slots * slot_bytes);
+        while (full > 1 && (size_t)full * slot_bytes > budget) --full;
+        const int slots = std::min(n_glob, full);
+        int rc = ensure_gscratch(w, (size_t)full * slot_bytes);
         if (rc) return rc;
         a.list = w.lists + (size_t)kGlobalTier * shots;
         a.count = w.small + kGlobalTier;
@@ -707,7 +710,11 @@ namespace {
 
 int srv_run_batch(bp4m_server* S, SrvSlot& sl, std::vector<SrvRequest*>& batch, int64_t n, int64_t stamp) {
     SrvRequest& h = *batch[0];
-    bp4m_graph* g = S->graphs[h.graph];
+    bp4m_graph* g = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);  // bp4m_server_add_graph may grow the list
+        g = S->graphs[h.graph];
+    }
     const int ty = g->host.n_types == 2 ? h.opts.type : 0;
     const int nw = n_words_of(g, ty);
     cudaStream_t st = sl.st;
@@ -716,11 +723,16 @@ int srv_run_batch(bp4m_server* S, SrvSlot& sl, std::vector<SrvRequest*>& batch, 
     const size_t before = it == sl.ws.end() ? 0 : ws_bytes(it->second);
     Workspace& w = sl.ws[h.graph];
     sl.last_use[h.graph] = stamp;
-    if (w.cap < n && S->budget > 0) {
-        // bytes of the per-shot buffers at capacity n (ensure_ws) beyond what this workspace holds
+    // per-shot buffers are sized for a full batch at once: a workspace that grew request by
+    // request would free and reallocate device memory (a device-wide synchronisation that
+    // stalls every other slot) each time a larger request arrived
+    const int64_t cap = std::max<int64_t>(n, S->max_batch);
+    if (w.cap < cap && S->budget > 0) {
+        // bytes of the per-shot buffers at that capacity (ensure_ws) beyond what this
+        // workspace holds
         size_t words = 0;
         for (int t = 0; t < g->host.n_types; ++t) words += n_words_of(g, t);
-        const int64_t need = (int64_t)((size_t)n * (words * 4 + 5 * g->host.n_types + kTiers * 4)) - (int64_t)before;
+        const int64_t need = (int64_t)((size_t)cap * (words * 4 + 5 * g->host.n_types + kTiers * 4)) - (int64_t)before;
         while (S->used.load() + need > S->budget) {
             int victim = -1;
             int64_t oldest = INT64_MAX;
@@ -738,17 +750,21 @@ int srv_run_batch(bp4m_server* S, SrvSlot& sl, std::vector<SrvRequest*>& batch, 
             ++S->evictions;
         }
     }
-    int rc = ensure_ws(g, w, std::max<int64_t>(n, w.cap));
+    int rc = ensure_ws(g, w, std::max<int64_t>(cap, w.cap));
     if (rc) return rc;
-    // pinned staging
+    // pinned staging, sized for the widest syndrome row of the server's graphs
     if (sl.h_cap < n || sl.h_words < nw) {
         cudaFreeHost(sl.h_in);
         cudaFreeHost(sl.h_out);
         sl.h_in = nullptr;
         sl.h_out = nullptr;
         sl.h_cap = 0;
-        const int64_t cap = std::max<int64_t>(n, S->max_batch);
-        const int64_t words = std::max<int64_t>(nw, sl.h_words);
+        int64_t words = std::max<int64_t>(nw, sl.h_words);
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            for (bp4m_graph* gg : S->graphs)
+                for (int t = 0; t < gg->host.n_types; ++t) words = std::max<int64_t>(words, n_words_of(gg, t));
+        }
         CK(cudaMallocHost(reinterpret_cast<void**>(&sl.h_in), (size_t)cap * words * 4));
         CK(cudaMallocHost(reinterpret_cast<void**>(&sl.h_out), (size_t)cap * 2));
         sl.h_cap = cap;

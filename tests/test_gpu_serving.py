@@ -31,7 +31,9 @@ def _alone(g, synd, opts):
 @pytest.fixture(scope="module")
 def graphs():
     torch_cuda()
-    gs = [pkg.Graph(5, "circuit", 0.006), pkg.Graph(9, "circuit", 0.005), pkg.Graph(7, "code_capacity", 0.08)]
+    # d = 25 at p = 0.005 (about 900 defects a shot) runs in the streaming tier
+    gs = [pkg.Graph(5, "circuit", 0.006), pkg.Graph(9, "circuit", 0.005), pkg.Graph(7, "code_capacity", 0.08),
+          pkg.Graph(25, "circuit", 0.005)]
     yield gs
     for g in gs:
         g.close()
@@ -54,8 +56,8 @@ def test_mixed_requests_match_decode_alone(graphs):
         a = 2000 * k
         reqs.append((1, a, 2000))
     for _ in range(60):
-        k = int(rng.integers(0, 3))
-        n = int(rng.integers(1, 300))
+        k = int(rng.integers(0, 4))
+        n = int(rng.integers(1, 300 if k < 3 else 64))
         a = int(rng.integers(0, 6000 - n))
         reqs.append((k, a, n))
     outs = []
