@@ -680,6 +680,74 @@ size_t ws_bytes(const Workspace& w) {
     return (size_t)w.cap * (w.words_total * 4 + 5 * w.n_types) + (size_t)w.cap * kTiers * 4 + w.gscratch_bytes;
 }
 
+// Mean number of unsatisfied detectors of a shot of type ty: each detector is unsatisfied
+// when an odd number of its edges flip, with probability (1 - prod_e (1 - 2 q_e)) / 2
+// (circuit edges carry their merged q; a code-capacity edge flips with 2p/3).
+double expected_defects(const bp4m_graph* g, int ty) {
+    const TypeTables& t = g->host.t[ty];
+    std::vector<double> prod((size_t)t.n_det, 1.0);
+    for (const Edge& e : t.edges) {
+        const double q = g->host.model == BP4M_CIRCUIT ? e.q : 2.0 * g->host.p / 3.0;
+        prod[(size_t)e.u] *= 1.0 - 2.0 * q;
+        if (e.v < t.n_det) prod[(size_t)e.v] *= 1.0 - 2.0 * q;
+    }
+    double m = 0.0;
+    for (double x : prod) m += 0.5 * (1.0 - x);
+    return m;
+}
+
+// Admission of batches to the GPU: shared batches run together, an exclusive batch runs
+// alone.  Waiting exclusive batches go first (a stream of shared batches cannot starve
+// them).
+class GpuGate {
+public:
+    void lock_shared() {
+        std::unique_lock<std::mutex> lk(m_);
+        cv_.wait(lk, [&] { return !excl_ && excl_waiting_ == 0; });
+        ++shared_;
+    }
+    void unlock_shared() {
+        std::lock_guard<std::mutex> lk(m_);
+        if (--shared_ == 0) cv_.notify_all();
+    }
+    void lock() {
+        std::unique_lock<std::mutex> lk(m_);
+        ++excl_waiting_;
+        cv_.wait(lk, [&] { return !excl_ && shared_ == 0; });
+        --excl_waiting_;
+        excl_ = true;
+    }
+    void unlock() {
+        std::lock_guard<std::mutex> lk(m_);
+        excl_ = false;
+        cv_.notify_all();
+    }
+
+private:
+    std::mutex m_;
+    std::condition_variable cv_;
+    int shared_ = 0, excl_waiting_ = 0;
+    bool excl_ = false;
+};
+
+// Holds the gate for one batch (exclusive or shared) until it goes out of scope.
+struct GateHold {
+    GpuGate& g;
+    bool excl;
+    GateHold(GpuGate& g_, bool excl_) : g(g_), excl(excl_) {
+        if (excl)
+            g.lock();
+        else
+            g.lock_shared();
+    }
+    ~GateHold() {
+        if (excl)
+            g.unlock();
+        else
+            g.unlock_shared();
+    }
+};
+
 bool same_batch(const SrvRequest& a, const SrvRequest& b) {
     return a.graph == b.graph && a.iters == b.iters && a.opts.precision == b.opts.precision &&
            a.opts.early_exit == b.opts.early_exit && a.opts.decoder == b.opts.decoder &&
@@ -690,6 +758,13 @@ bool same_batch(const SrvRequest& a, const SrvRequest& b) {
 
 struct bp4m_server {
     std::vector<bp4m_graph*> graphs;
+    // per graph: its shots average more unsatisfied detectors than the shared-memory tiers
+    // hold, so a batch runs in the streaming tier and fills the GPU by itself
+    std::vector<char> heavy;
+    // heavy batches run alone: concurrent streaming-tier launches of several slots were
+    // measured to lose up to 3x of the throughput of running them one after another, so a
+    // heavy batch holds this gate exclusively and every other batch holds it shared
+    GpuGate gate;
     int device = -1;
     int64_t max_batch = 4096;
     int64_t budget = 0;
@@ -711,10 +786,13 @@ namespace {
 int srv_run_batch(bp4m_server* S, SrvSlot& sl, std::vector<SrvRequest*>& batch, int64_t n, int64_t stamp) {
     SrvRequest& h = *batch[0];
     bp4m_graph* g = nullptr;
+    bool heavy = false;
     {
         std::lock_guard<std::mutex> lk(S->mu);  // bp4m_server_add_graph may grow the list
         g = S->graphs[h.graph];
+        heavy = S->heavy[h.graph] != 0;
     }
+    GateHold hold(S->gate, heavy);
     const int ty = g->host.n_types == 2 ? h.opts.type : 0;
     const int nw = n_words_of(g, ty);
     cudaStream_t st = sl.st;
@@ -1042,8 +1120,11 @@ int bp4m_server_add_graph(bp4m_server* S, bp4m_graph* g) {
             CK(prepare_decode_kernels(prec));
             g->prepared[prec] = true;
         }
+    double m = 0.0;
+    for (int ty = 0; ty < g->host.n_types; ++ty) m = std::max(m, expected_defects(g, ty));
     std::lock_guard<std::mutex> lk(S->mu);
     S->graphs.push_back(g);
+    S->heavy.push_back(m > 160.0 ? 1 : 0);
     return (int)S->graphs.size() - 1;
 }
 
