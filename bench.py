@@ -62,10 +62,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     # message storage: fp32 (the configuration's, default) or the 16-bit forms (FP32 math)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
-    # decoding-service measurement: circuit graphs of these distances (p = 0.005), requests
-    # of 1..4096 shots arriving as a Poisson process at a fraction of the measured capacity
-    ap.add_argument("--serve-d", default="5,9,13")
-    ap.add_argument("--serve-requests", type=int, default=400)
+    # decoding-service measurement: circuit graphs of these distances (p = 0.005; the
+    # default is every odd distance 5..25), requests of 1..4096 shots arriving as a Poisson
+    # process at a fraction of the measured capacity
+    ap.add_argument("--serve-d", default="5,7,9,11,13,15,17,19,21,23,25")
+    # a second mix of small distances only, where every batch fits the shared-memory tiers
+    ap.add_argument("--serve-d-low", default="5,9,13")
+    ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-load", type=float, default=0.5)
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--no-serve", action="store_true")
@@ -180,7 +183,7 @@ def cpu_baseline(n_shots=None, seed=SEED, first_shot=0):
 
 # ---------------------------------------------------------------- our arm
 
-def run_serving(args, dev):
+def run_serving(args, dev, serve_d):
     """p50/p99 request latency and sustained shots/s of the decoding service (Server) on a
     Poisson stream of requests of mixed distance: each request a uniform 1..4096-shot slice
     of pre-sampled syndromes of one of the graphs.  Capacity is measured first by a closed
@@ -189,7 +192,7 @@ def run_serving(args, dev):
     import torch
     import paper_2603_05381_gb300 as pkg
 
-    ds = [int(x) for x in args.serve_d.split(",") if x]
+    ds = [int(x) for x in serve_d.split(",") if x]
     rng = np.random.default_rng(SEED)
     opts = pkg.make_opts(precision=args.precision, early_exit=True)
     graphs, pools = [], []
@@ -212,8 +215,8 @@ def run_serving(args, dev):
         a = int(rng.integers(0, 8192 - n + 1))
         return k, np.ascontiguousarray(pools[k][a:a + n]), np.empty(n, dtype=np.uint8)
 
-    # warm-up: every graph once in every slot
-    warm = [make_request() for _ in range(4 * len(graphs) * args.serve_slots)]
+    # warm-up: workspaces of every graph in the slots (two random requests per graph and slot)
+    warm = [make_request() for _ in range(2 * len(graphs) * args.serve_slots)]
     for r in [srv.submit(gids[k], s, T, opts, o) for k, s, o in warm]:
         srv.wait(r)
     # capacity: a closed burst
@@ -472,7 +475,10 @@ def run_ours(args, rank, world, local):
         "gpu_launches": launches,
     }
     if rank == 0 and not args.no_serve:
-        line["serving"] = run_serving(args, dev)
+        if args.serve_d:
+            line["serving"] = run_serving(args, dev, args.serve_d)
+        if args.serve_d_low:
+            line["serving_low_d"] = run_serving(args, dev, args.serve_d_low)
     if rank == 0 and args.fused:
         line["fused"] = run_fused(args, dev)
     if rank == 0 and not args.no_cpu_baseline:
