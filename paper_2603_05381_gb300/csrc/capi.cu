@@ -88,6 +88,9 @@ struct Workspace {
     unsigned long long* host_ctr = nullptr;
     void* gscratch = nullptr;
     size_t gscratch_bytes = 0;
+    int32_t* sub = nullptr;       // [kMaxGlobalClasses][sub_cap]: global-tier items by width class
+    int32_t* subctr = nullptr;    // counts[kMaxGlobalClasses], next[kMaxGlobalClasses]
+    int64_t sub_cap = 0;
     cudaEvent_t ev_small = nullptr;
     // B-BP4MF first stage
     int64_t qcap = 0;
@@ -313,6 +316,8 @@ void free_ws(Workspace& w) {
     cudaFree(w.small);
     cudaFree(w.ctr);
     cudaFree(w.gscratch);
+    cudaFree(w.sub);
+    cudaFree(w.subctr);
     cudaFreeHost(w.host_small);
     cudaFreeHost(w.host_ctr);
     if (w.ev_small) cudaEventDestroy(w.ev_small);
@@ -359,6 +364,70 @@ int ensure_gscratch(Workspace& w, size_t bytes) {
     w.gscratch_bytes = 0;
     CK(cudaMalloc(&w.gscratch, bytes));
     w.gscratch_bytes = bytes;
+    return BP4M_OK;
+}
+
+int ensure_split(Workspace& w, int64_t cap) {
+    if (w.sub_cap >= cap) return BP4M_OK;
+    cudaFree(w.sub);
+    cudaFree(w.subctr);
+    w.sub = nullptr;
+    w.subctr = nullptr;
+    w.sub_cap = 0;
+    CK(dalloc(&w.sub, (size_t)kMaxGlobalClasses * cap));
+    CK(dalloc(&w.subctr, 2 * kMaxGlobalClasses));
+    w.sub_cap = cap;
+    return BP4M_OK;
+}
+
+// Scratch of the global tier split into width classes: per class its slot size, the slot
+// count (one per resident block, bounded by 16 GB) and the scratch bytes of the widest need.
+struct GlobalPlan {
+    GlobalClasses gc;
+    size_t slot_bytes[kMaxGlobalClasses];
+    int gsmax[kMaxGlobalClasses];
+    int full[kMaxGlobalClasses];
+    size_t need = 0;
+};
+
+GlobalPlan global_plan(int prec, int max_s, int num_sms) {
+    GlobalPlan p;
+    p.gc = global_classes(prec, max_s);
+    const size_t budget = (size_t)16 << 30;
+    for (int c = 0; c < p.gc.n; ++c) {
+        p.slot_bytes[c] = global_slot_bytes(prec, p.gc.smax[c], &p.gsmax[c]);
+        int full = num_sms * global_blocks_per_sm(prec, p.gc.smax[c]);
+        while (full > 1 && (size_t)full * p.slot_bytes[c] > budget) --full;
+        p.full[c] = full;
+        p.need = std::max(p.need, (size_t)full * p.slot_bytes[c]);
+    }
+    return p;
+}
+
+// Launches the global tier (list a.list, device count a.count) class by class: one launch
+// when a single class can occur, else a partition of the list and one launch per class.
+// `items` bounds the tier's count; `stride` is the per-class list capacity in w_sub.
+int launch_global_classes(DecodeArgs a, const GlobalPlan& p, int prec, int64_t items, int32_t* w_sub,
+                          int32_t* w_subctr, int64_t stride, int32_t* next_single, int num_sms, cudaStream_t st) {
+    const size_t esz = prec == 0 ? sizeof(double) : sizeof(float);
+    if (p.gc.n == 1) {
+        a.next = next_single;
+        a.gslot_elems = (int64_t)(p.slot_bytes[0] / esz / 3);
+        a.gsmax = p.gsmax[0];
+        CK(launch_decode_global(prec, a, (int)std::min<int64_t>(items, p.full[0]), st));
+        return BP4M_OK;
+    }
+    CK(cudaMemsetAsync(w_subctr, 0, 2 * kMaxGlobalClasses * sizeof(int32_t), st));
+    CK(launch_partition_global(a, p.gc, w_sub, stride, w_subctr, items, num_sms, st));
+    for (int c = 0; c < p.gc.n; ++c) {
+        DecodeArgs b = a;
+        b.list = w_sub + (size_t)c * stride;
+        b.count = w_subctr + c;
+        b.next = w_subctr + kMaxGlobalClasses + c;
+        b.gslot_elems = (int64_t)(p.slot_bytes[c] / esz / 3);
+        b.gsmax = p.gsmax[c];
+        CK(launch_decode_global(prec, b, (int)std::min<int64_t>(items, p.full[c]), st));
+    }
     return BP4M_OK;
 }
 
@@ -501,25 +570,25 @@ int decode_device(bp4m_graph* g, Workspace& w, int ty, const uint32_t* synd, int
     const int n_glob = w.host_small[kGlobalTier];
     if (n_glob > 0) {
         const int max_s = w.host_small[2 * kTiers];
-        int gsmax = 0;
-        const size_t slot_bytes = global_slot_bytes(prec, max_s, &gsmax);
-        // the scratch holds a slot for every resident block, whatever this batch's count, so
+        // width classes up to the batch's largest defect count; the scratch holds a slot for
+        // every resident block of the class that needs most, whatever this batch's count, so
         // that it is reallocated (a device-wide synchronisation) only for a wider slot
-        int full = g->num_sms * global_blocks_per_sm(prec, max_s);
-        const size_t budget = (size_t)16 << 30;
-        while (full > 1 && (size_t)full * slot_bytes > budget) --full;
-        const int slots = std::min(n_glob, full);
-        int rc = ensure_gscratch(w, (size_t)full * slot_bytes);
+        const GlobalPlan p = global_plan(prec, max_s, g->num_sms);
+        int rc = ensure_gscratch(w, p.need);
         if (rc) return rc;
+        if (p.gc.n > 1) {
+            rc = ensure_split(w, shots);
+            if (rc) return rc;
+        }
         a.list = w.lists + (size_t)kGlobalTier * shots;
         a.count = w.small + kGlobalTier;
-        a.next = w.small + kTiers + kGlobalTier;
         a.gscratch = w.gscratch;
-        a.gslot_elems = (int64_t)(slot_bytes / (prec == 0 ? sizeof(double) : sizeof(float)) / 3);
-        a.gsmax = gsmax;
+        a.gscratch_bytes = (int64_t)w.gscratch_bytes;
         a.tier = kGlobalTier;
         ProfScope ps(g, PROF_GLOBAL, st);
-        CK(launch_decode_global(prec, a, slots, st));
+        rc = launch_global_classes(a, p, prec, n_glob, w.sub, w.subctr, shots, w.small + kTiers + kGlobalTier,
+                                   g->num_sms, st);
+        if (rc) return rc;
         ps.end();
     }
     return BP4M_OK;
@@ -978,9 +1047,8 @@ struct bp4m_multi {
     unsigned long long* ctr = nullptr;
     unsigned long long* h_ctr = nullptr;
     void* gscratch = nullptr;
-    size_t gslot_bytes = 0;
-    int gsmax = 0;
-    int gslots = 0;
+    int32_t* sub = nullptr;       // [kMaxGlobalClasses][total_cap]
+    int32_t* subctr = nullptr;
     cudaStream_t st = nullptr;
     int plan = 0;
     bool tuned = false;
@@ -1008,6 +1076,8 @@ void multi_free(bp4m_multi* m) {
     cudaFree(m->ctr);
     cudaFreeHost(m->h_ctr);
     cudaFree(m->gscratch);
+    cudaFree(m->sub);
+    cudaFree(m->subctr);
     if (m->exec) cudaGraphExecDestroy(m->exec);
     if (m->st) cudaStreamDestroy(m->st);
     delete m;
@@ -1050,12 +1120,15 @@ int multi_enqueue(bp4m_multi* m, const std::vector<int64_t>& shots, int plan) {
     }
     a.list = m->lists + (size_t)kGlobalTier * m->total_cap;
     a.count = m->small + kGlobalTier;
-    a.next = m->small + kTiers + kGlobalTier;
     a.tier = kGlobalTier;
     a.gscratch = m->gscratch;
-    a.gslot_elems = (int64_t)(m->gslot_bytes / sizeof(float) / 3);
-    a.gsmax = m->gsmax;
-    CK(launch_decode_global(1, a, m->gslots, st));
+    {
+        // every width class up to max_defects: the counts stay on the device
+        const GlobalPlan p = global_plan(1, m->max_defects, m->num_sms);
+        const int rc = launch_global_classes(a, p, 1, m->total_cap, m->sub, m->subctr, m->total_cap,
+                                             m->small + kTiers + kGlobalTier, m->num_sms, st);
+        if (rc) return rc;
+    }
     for (int k = 0; k < n; ++k) {
         const MultiHostEntry& x = m->e[k];
         if (shots[k] <= 0) continue;
@@ -1307,11 +1380,15 @@ bp4m_multi* bp4m_multi_create(int n, bp4m_graph* const* graphs, const int* types
         return bad(fail(BP4M_ENOMEM, "out of memory for the fused decode's lists"));
     if (cudaMemcpy(m->d_entries, host.data(), sizeof(MultiEntry) * n, cudaMemcpyHostToDevice) != cudaSuccess)
         return bad(fail(BP4M_ECUDA, "upload of the entries failed"));
-    // streaming tier: one slot per resident block, sized for max_defects
-    m->gslot_bytes = global_slot_bytes(1, max_defects, &m->gsmax);
-    m->gslots = (int)std::min<int64_t>(m->total_cap, (int64_t)m->num_sms * global_blocks_per_sm(1, max_defects));
-    if (cudaMalloc(&m->gscratch, m->gslot_bytes * m->gslots) != cudaSuccess)
-        return bad(fail(BP4M_ENOMEM, "out of memory for the streaming tier's scratch"));
+    // streaming tier: per width class up to max_defects one slot per resident block
+    {
+        const GlobalPlan p = global_plan(1, max_defects, m->num_sms);
+        if (cudaMalloc(&m->gscratch, p.need) != cudaSuccess)
+            return bad(fail(BP4M_ENOMEM, "out of memory for the streaming tier's scratch"));
+        if (dalloc(&m->sub, (size_t)kMaxGlobalClasses * m->total_cap) != cudaSuccess ||
+            dalloc(&m->subctr, 2 * kMaxGlobalClasses) != cudaSuccess)
+            return bad(fail(BP4M_ENOMEM, "out of memory for the streaming tier's lists"));
+    }
     if (cudaStreamCreateWithFlags(&m->st, cudaStreamNonBlocking) != cudaSuccess)
         return bad(fail(BP4M_ECUDA, "cudaStreamCreate failed"));
     return m;

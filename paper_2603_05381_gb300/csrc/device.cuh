@@ -218,6 +218,20 @@ size_t global_slot_bytes(int precision, int max_s, int* gsmax_out);
 int global_blocks_per_sm(int precision, int max_s);
 cudaError_t launch_decode_global(int precision, const DecodeArgs& a, int slots,
                                  cudaStream_t st);
+// Width classes of the global tier for a batch whose largest defect count is max_s: class k
+// takes the shots with smax[k-1] < s <= smax[k] (smax ascending; the last class is max_s's
+// own, the general kernel's when max_s is above the widest streaming variant).
+constexpr int kMaxGlobalClasses = 12;
+struct GlobalClasses {
+    int n;
+    int smax[kMaxGlobalClasses];
+};
+GlobalClasses global_classes(int precision, int max_s);
+// Splits the global tier's list (a.list, a.count) into the classes' lists: class k's items go
+// to sub[k * stride ..], its count to sub_counts[k] (zeroed by the caller); a shot above the
+// last bound goes to the last class.  max_items bounds a.count (sizes the grid).
+cudaError_t launch_partition_global(const DecodeArgs& a, const GlobalClasses& gc, int32_t* sub, int64_t stride,
+                                    int32_t* sub_counts, int64_t max_items, int num_sms, cudaStream_t st);
 // Shared-memory tier plan for a precision.
 TierPlan tier_plan(int precision);
 cudaError_t prepare_decode_kernels(int precision);

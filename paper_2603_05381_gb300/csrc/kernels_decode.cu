@@ -3,7 +3,9 @@
 // The shared-memory kernel and its tier table are in decode_smem.cuh.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
+#include <initializer_list>
 #include <cfloat>
 #include <cmath>
 
@@ -921,7 +923,8 @@ int stream_ch(int precision, int max_s) {
 }  // namespace
 
 int global_blocks_per_sm(int precision, int max_s) {
-    return (precision != 0 && stream_ch(precision, max_s) <= 8) ? kStreamBlocks<float, 8> : 1;
+    const int ch = stream_ch(precision, max_s);
+    return (precision != 0 && ch != 0 && ch <= 8) ? kStreamBlocks<float, 8> : 1;
 }
 
 size_t global_slot_bytes(int precision, int max_s, int* gsmax_out) {
@@ -969,6 +972,69 @@ cudaError_t launch_decode_global(int precision, const DecodeArgs& a, int slots, 
         if (e != cudaSuccess) return e;
         decode_global_kernel<float><<<slots, kGlobThreads, smem, st>>>(a);
     }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ width classes
+//
+// The streaming kernel's width follows the largest defect count it may meet, and its work
+// per shot is s rows x width columns, so one shot far above the others would widen the
+// whole global tier.  The tier is therefore split by width: class k takes the shots with
+// smax[k-1] < s <= smax[k] and runs at its own width.
+
+GlobalClasses global_classes(int precision, int max_s) {
+    GlobalClasses gc{};
+    int widths[kMaxGlobalClasses];
+    int nw = 0;
+    if (precision != 0) {
+        for (int ch : {6, 8, 10, 12, 14, 16, 20, 24, 28, 32}) widths[nw++] = 32 * ch;
+    } else {
+        widths[nw++] = 256;
+        widths[nw++] = 512;
+    }
+    for (int k = 0; k < nw; ++k) {
+        gc.smax[gc.n++] = widths[k];
+        if (max_s <= widths[k]) return gc;
+    }
+    gc.smax[gc.n++] = max_s;  // the general kernel takes everything above the widest variant
+    return gc;
+}
+
+namespace {
+
+constexpr int kPartThreads = 256;
+
+__global__ void __launch_bounds__(kPartThreads) partition_global_kernel(const DecodeArgs a, GlobalClasses gc,
+                                                                        int32_t* sub, int64_t stride,
+                                                                        int32_t* sub_counts) {
+    const int64_t count = a.count ? (int64_t)*a.count : a.count_val;
+    for (int64_t i = (int64_t)blockIdx.x * kPartThreads + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * kPartThreads) {
+        const int32_t code = a.list[i];
+        const ItemCtx ic = resolve_item(a, code);
+        const uint32_t* w = ic.synd + (size_t)ic.shot * ic.tb.n_words;
+        int sdef = 0;
+        for (int k = 0; k < ic.tb.n_words; ++k) sdef += __popc(__ldg(w + k));
+        // a shot above the last bound goes to the last class, whose kernel reports it
+        int c = gc.n - 1;
+        for (int k = 0; k < gc.n; ++k)
+            if (sdef <= gc.smax[k]) {
+                c = k;
+                break;
+            }
+        const int pos = atomicAdd(sub_counts + c, 1);
+        sub[(size_t)c * stride + pos] = code;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_partition_global(const DecodeArgs& a, const GlobalClasses& gc, int32_t* sub, int64_t stride,
+                                    int32_t* sub_counts, int64_t max_items, int num_sms, cudaStream_t st) {
+    if (max_items <= 0) return cudaSuccess;
+    const int64_t want = (max_items + kPartThreads - 1) / kPartThreads;
+    const int grid = (int)std::min<int64_t>(want, (int64_t)num_sms * 8);
+    partition_global_kernel<<<grid, kPartThreads, 0, st>>>(a, gc, sub, stride, sub_counts);
     return cudaGetLastError();
 }
 
