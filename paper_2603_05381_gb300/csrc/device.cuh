@@ -212,9 +212,10 @@ constexpr int kRwMaxTier64 = 3;
 // weights <= 0, for which shortest paths do not exist on an undirected graph.
 constexpr double kRwMinWeight = 9.5367431640625e-07;  // 2^-20
 // Global-memory tier.  `slots` CTAs each own one scratch slot of global_slot_bytes() for
-// the batch's largest defect count; a.gsmax must be the value that function reports.
+// shots of up to max_s defects (a width class's bound); a.gsmax must be the value that
+// function reports.
 size_t global_slot_bytes(int precision, int max_s, int* gsmax_out);
-// Resident blocks per SM of the global-memory tier for the batch's largest defect count.
+// Resident blocks per SM of the global-memory tier for shots of up to max_s defects.
 int global_blocks_per_sm(int precision, int max_s);
 cudaError_t launch_decode_global(int precision, const DecodeArgs& a, int slots,
                                  cudaStream_t st);

@@ -318,7 +318,6 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
 // (lambda of the previous update, convergence vote, candidates / forced convergence), then
 // the update pass.
 constexpr int kStreamWarps = 16;
-constexpr int kStreamThreads = kStreamWarps * 32;
 // Blocks per SM: the 256-column variant (shots of up to 256 defects) runs two, so that one
 // block's L2 latency overlaps the other's arithmetic.
 template <typename T, int CH>
@@ -896,8 +895,8 @@ cudaError_t run_stream(const DecodeArgs& a, int slots, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Columns per lane of the streaming kernel for the largest defect count of a batch; 0 when
-// the general global kernel takes the batch.
+// Columns per lane of the streaming kernel for shots of up to max_s defects; 0 when the
+// general global kernel takes them.
 // FP32 steps of 64 columns up to 512 and of 128 columns up to 1024 keep the padding of a
 // shot of more than 160 defects below 1.3x in each dimension (d = 15..25 circuits at
 // p = 0.005 average 194, 283, 395, 534, 702 and 902 defects).
