@@ -255,12 +255,16 @@ void bp4m_free_graph(bp4m_graph* g);
    takes the oldest pending request and merges into it every pending request of the same
    graph, iterations and options while the merged batch stays within max_batch_shots
    (continuous batching); its host-to-device copy, decode kernels and device-to-host copy
-   run on its stream, so the slots' batches overlap on the GPU.  Message state and tables
-   stay resident: each slot keeps one workspace per graph it has decoded.  When the device
-   bytes of all workspaces' per-shot buffers would exceed device_budget_bytes (0: no limit),
-   a slot frees its least recently used workspaces before allocating; a batch that still
-   does not fit fails with BP4M_ENOMEM.  (Scratch of the global-memory tier, for shots
-   with more than 160 unsatisfied detectors, grows on demand outside the budget.)  A graph's per-iteration results are
+   run on its stream, so the slots' batches overlap on the GPU, except that a batch of a
+   heavy graph (one whose shots average more than 160 unsatisfied detectors, estimated
+   from its edge probabilities when it is added) runs alone: it waits for the batches in
+   flight and holds back new ones until it ends.  Message state and tables stay resident:
+   each slot keeps one workspace per graph it has decoded, sized for max_batch_shots.
+   When the device bytes of all workspaces' per-shot buffers would exceed
+   device_budget_bytes (0: no limit), a slot frees its least recently used workspaces
+   before allocating; a batch that still does not fit fails with BP4M_ENOMEM.  (Scratch
+   of the global-memory tier, for shots with more than 160 unsatisfied detectors, grows
+   on demand outside the budget.)  A graph's per-iteration results are
    bit-identical to bp4m_decode_batch on the same syndromes, alone or merged with others.
    bp4m_profile_* does not see the service's launches.  Decoders BP4M and BP4MF (any
    precision); B-BP4MF is BP4M_EUNSUPPORTED. */
