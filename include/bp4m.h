@@ -118,6 +118,10 @@ typedef struct {
     int rounds;
     double p;
     int64_t table_bytes;  /* device bytes of the per-graph tables once uploaded */
+    double mean_defects[2];  /* expected unsatisfied detectors per shot and type: the sum over
+                                detectors of the probability that an odd number of their edges
+                                flip, (1 - prod_e (1 - 2 q_e)) / 2 (circuit edges carry their
+                                merged q; a code-capacity edge flips with 2p/3) */
 } bp4m_graph_info_t;
 
 typedef struct bp4m_graph bp4m_graph;

@@ -91,7 +91,7 @@ class Graph:
         return {"n_types": gi.n_types, "n_det": list(gi.n_det)[:gi.n_types],
                 "n_words": list(gi.n_words)[:gi.n_types], "n_edges": list(gi.n_edges)[:gi.n_types],
                 "n_units": gi.n_units, "model": gi.model, "d": gi.d, "rounds": gi.rounds, "p": gi.p,
-                "table_bytes": gi.table_bytes}
+                "table_bytes": gi.table_bytes, "mean_defects": list(gi.mean_defects)[:gi.n_types]}
 
     def export(self, what, type=0):
         """Host copy of a table: 'W', 'L', 'parity', 'edges', 'thresholds'."""

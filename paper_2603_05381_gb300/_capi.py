@@ -54,7 +54,7 @@ class GraphInfo(ctypes.Structure):
     _fields_ = [("n_types", ctypes.c_int), ("n_det", ctypes.c_int * 2), ("n_words", ctypes.c_int * 2),
                 ("n_edges", ctypes.c_int * 2), ("n_units", ctypes.c_int), ("model", ctypes.c_int),
                 ("d", ctypes.c_int), ("rounds", ctypes.c_int), ("p", ctypes.c_double),
-                ("table_bytes", ctypes.c_int64)]
+                ("table_bytes", ctypes.c_int64), ("mean_defects", ctypes.c_double * 2)]
 
 
 class Edge(ctypes.Structure):

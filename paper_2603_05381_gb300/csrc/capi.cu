@@ -1520,6 +1520,7 @@ int bp4m_graph_info(const bp4m_graph* g, bp4m_graph_info_t* out) {
         tb += (int64_t)h.t[ty].n_det * h.t[ty].n_det * (int64_t)(sizeof(float) + 2 * sizeof(double) + 1);
     tb += h.model == BP4M_CIRCUIT ? (int64_t)h.n_units * 8 : (int64_t)h.n_units * 8;
     out->table_bytes = tb;
+    for (int ty = 0; ty < h.n_types; ++ty) out->mean_defects[ty] = expected_defects(g, ty);
     return BP4M_OK;
 }
 

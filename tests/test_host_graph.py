@@ -113,3 +113,32 @@ def test_unrotated_tables_match_oracle(lib, d):
         ct = code_capacity_tables(cg, 0.07)
         assert [(u, v, o) for (u, v, o, _) in g2.export("edges", ty)] == [(u, v, o) for (u, v, o, _) in cg.edges]
         assert np.array_equal(g2.export("W", ty), ct.W) and np.array_equal(g2.export("parity", ty), ct.P)
+
+
+def test_mean_defects_closed_form_and_oracle_edges(lib):
+    from paper_2603_05381_gb300 import Graph
+    # rotated code capacity: per type (d-1)^2/2 checks of weight 4 and d-1 of weight 2; a data
+    # qubit flips a check type with probability 2p/3, so a weight-w check is unsatisfied with
+    # probability (1 - (1 - 4p/3)^w) / 2
+    for d, p in ((5, 0.05), (9, 0.10), (21, 0.20)):
+        g = Graph(d, "code_capacity", p)
+        r = 1.0 - 4.0 * p / 3.0
+        want = ((d - 1) ** 2 / 2 * (1 - r ** 4) + (d - 1) * (1 - r ** 2)) / 2
+        got = g.info()["mean_defects"]
+        assert len(got) == 2
+        for x in got:
+            assert abs(x - want) <= 1e-12 * want
+        g.close()
+    # circuits: the same sum over the oracle's merged edges
+    for d, p in ((5, 0.008), (13, 0.005)):
+        g = Graph(d, "circuit", p)
+        og, _, _ = circuit_graph(d, Noise(p))
+        prod = np.ones(og.n_det)
+        for (u, v, _, q) in og.edges:
+            prod[u] *= 1 - 2 * q
+            if v < og.n_det:
+                prod[v] *= 1 - 2 * q
+        want = float(((1 - prod) / 2).sum())
+        got = g.info()["mean_defects"][0]
+        assert abs(got - want) <= 1e-9 * want
+        g.close()
