@@ -91,6 +91,9 @@ struct Workspace {
     int32_t* sub = nullptr;       // [kMaxGlobalClasses][sub_cap]: global-tier items by width class
     int32_t* subctr = nullptr;    // counts[kMaxGlobalClasses], next[kMaxGlobalClasses]
     int64_t sub_cap = 0;
+    int32_t* host_sub = nullptr;  // pinned mirror of the class counts
+    cudaStream_t aux = nullptr;   // second stream: classes of few shots run beside the others
+    cudaEvent_t ev_sub = nullptr, ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev_small = nullptr;
     // B-BP4MF first stage
     int64_t qcap = 0;
@@ -318,6 +321,11 @@ void free_ws(Workspace& w) {
     cudaFree(w.gscratch);
     cudaFree(w.sub);
     cudaFree(w.subctr);
+    cudaFreeHost(w.host_sub);
+    if (w.aux) cudaStreamDestroy(w.aux);
+    if (w.ev_sub) cudaEventDestroy(w.ev_sub);
+    if (w.ev_fork) cudaEventDestroy(w.ev_fork);
+    if (w.ev_join) cudaEventDestroy(w.ev_join);
     cudaFreeHost(w.host_small);
     cudaFreeHost(w.host_ctr);
     if (w.ev_small) cudaEventDestroy(w.ev_small);
@@ -377,6 +385,11 @@ int ensure_split(Workspace& w, int64_t cap) {
     CK(dalloc(&w.sub, (size_t)kMaxGlobalClasses * cap));
     CK(dalloc(&w.subctr, 2 * kMaxGlobalClasses));
     w.sub_cap = cap;
+    if (!w.host_sub) CK(cudaMallocHost(reinterpret_cast<void**>(&w.host_sub), kMaxGlobalClasses * sizeof(int32_t)));
+    if (!w.aux) CK(cudaStreamCreateWithFlags(&w.aux, cudaStreamNonBlocking));
+    if (!w.ev_sub) CK(cudaEventCreateWithFlags(&w.ev_sub, cudaEventDisableTiming));
+    if (!w.ev_fork) CK(cudaEventCreateWithFlags(&w.ev_fork, cudaEventDisableTiming));
+    if (!w.ev_join) CK(cudaEventCreateWithFlags(&w.ev_join, cudaEventDisableTiming));
     return BP4M_OK;
 }
 
@@ -387,7 +400,8 @@ struct GlobalPlan {
     size_t slot_bytes[kMaxGlobalClasses];
     int gsmax[kMaxGlobalClasses];
     int full[kMaxGlobalClasses];
-    size_t need = 0;
+    size_t need = 0;        // the largest class with a slot per resident block
+    size_t need_small = 0;  // a class of fewer shots than half its resident blocks
 };
 
 GlobalPlan global_plan(int prec, int max_s, int num_sms) {
@@ -400,7 +414,9 @@ GlobalPlan global_plan(int prec, int max_s, int num_sms) {
         while (full > 1 && (size_t)full * p.slot_bytes[c] > budget) --full;
         p.full[c] = full;
         p.need = std::max(p.need, (size_t)full * p.slot_bytes[c]);
+        p.need_small = std::max(p.need_small, (size_t)((full + 1) / 2) * p.slot_bytes[c]);
     }
+    p.need = (p.need + 255) / 256 * 256;
     return p;
 }
 
@@ -574,7 +590,7 @@ int decode_device(bp4m_graph* g, Workspace& w, int ty, const uint32_t* synd, int
         // every resident block of the class that needs most, whatever this batch's count, so
         // that it is reallocated (a device-wide synchronisation) only for a wider slot
         const GlobalPlan p = global_plan(prec, max_s, g->num_sms);
-        int rc = ensure_gscratch(w, p.need);
+        int rc = ensure_gscratch(w, p.need + (p.gc.n > 1 ? p.need_small : 0));
         if (rc) return rc;
         if (p.gc.n > 1) {
             rc = ensure_split(w, shots);
@@ -586,9 +602,42 @@ int decode_device(bp4m_graph* g, Workspace& w, int ty, const uint32_t* synd, int
         a.gscratch_bytes = (int64_t)w.gscratch_bytes;
         a.tier = kGlobalTier;
         ProfScope ps(g, PROF_GLOBAL, st);
-        rc = launch_global_classes(a, p, prec, n_glob, w.sub, w.subctr, shots, w.small + kTiers + kGlobalTier,
-                                   g->num_sms, st);
-        if (rc) return rc;
+        if (p.gc.n == 1) {
+            rc = launch_global_classes(a, p, prec, n_glob, w.sub, w.subctr, shots, w.small + kTiers + kGlobalTier,
+                                       g->num_sms, st);
+            if (rc) return rc;
+        } else {
+            // partition, then read the class counts: a class of fewer shots than half its
+            // resident blocks (typically a few shots above the bulk's width) runs on the
+            // second stream beside the others with its own scratch, instead of holding the
+            // stream for a whole shot's decode on a few SMs; empty classes are skipped
+            const size_t esz = prec == 0 ? sizeof(double) : sizeof(float);
+            CK(cudaMemsetAsync(w.subctr, 0, 2 * kMaxGlobalClasses * sizeof(int32_t), st));
+            CK(launch_partition_global(a, p.gc, w.sub, shots, w.subctr, n_glob, g->num_sms, st));
+            CK(cudaMemcpyAsync(w.host_sub, w.subctr, p.gc.n * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            CK(cudaEventRecord(w.ev_sub, st));
+            CK(cudaEventSynchronize(w.ev_sub));
+            CK(cudaEventRecord(w.ev_fork, st));
+            CK(cudaStreamWaitEvent(w.aux, w.ev_fork, 0));
+            // small classes first, so that their few blocks hold their SMs before the large
+            // classes' persistent blocks fill the rest
+            for (int pass = 0; pass < 2; ++pass)
+                for (int c = 0; c < p.gc.n; ++c) {
+                    const int cnt = w.host_sub[c];
+                    const bool small = 2 * cnt < p.full[c];
+                    if (cnt <= 0 || small != (pass == 0)) continue;
+                    DecodeArgs b = a;
+                    b.list = w.sub + (size_t)c * shots;
+                    b.count = w.subctr + c;
+                    b.next = w.subctr + kMaxGlobalClasses + c;
+                    b.gslot_elems = (int64_t)(p.slot_bytes[c] / esz / 3);
+                    b.gsmax = p.gsmax[c];
+                    if (small) b.gscratch = static_cast<unsigned char*>(w.gscratch) + p.need;
+                    CK(launch_decode_global(prec, b, small ? cnt : std::min(cnt, p.full[c]), small ? w.aux : st));
+                }
+            CK(cudaEventRecord(w.ev_join, w.aux));
+            CK(cudaStreamWaitEvent(st, w.ev_join, 0));
+        }
         ps.end();
     }
     return BP4M_OK;
