@@ -45,11 +45,10 @@ METRIC = "decoded shots/s & msg-updates/s vs HBM roofline (d=13 circuit); p50/p9
 WORKLOAD = "rotated surface code memory-Z circuit, d=13, 13 rounds, uniform depolarizing p=0.005 " \
            "(gates, idles, data before rounds, reset/measure flips); 10^6 shots per step; BP4M, " \
            "FP32 messages, T=50 with early exit and forced-convergence fallback"
-# MUFU (SFU) throughput per SM per clock on GB300, measured with dependent-free ex2/lg2
-# chains: ex2 32, lg2 16, and an alternating ex2+lg2 mix 21.3 results (10.67 pairs).  A
-# message update needs one ex2 and one lg2, i.e. 1/32 + 1/16 = 3/32 SM-cycles.
-MSG_PER_SM_PER_CLK = 32.0 / 3.0
-NUM_SMS = 152
+# The roofline denominator of the shared-memory tiers is measured in the same run by
+# bp4m_probe_mufu (profiles/mufu_peak.md): ex2 and lg2 results per SM per clock, and the
+# SM count of the device.  A message update needs one ex2 and one lg2, so it costs
+# 1/ex2 + 1/lg2 SM-cycles of the special-function unit.
 
 
 def parse():
@@ -76,6 +75,9 @@ def parse():
     # uneven shot counts, FP16/BF16/FP32 messages against the plain per-graph FP32 form
     ap.add_argument("--fused", action="store_true")
     ap.add_argument("--fused-scale", type=float, default=1.0)
+    # only measure the special-function unit (the shared-memory tiers' roofline
+    # denominator) with the SM clocks sampled meanwhile, print it and exit
+    ap.add_argument("--mufu-probe", action="store_true")
     return ap.parse_args()
 
 
@@ -340,6 +342,7 @@ def run_ours(args, rank, world, local):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+    mufu = pkg.probe_mufu()
     g = pkg.Graph(D, "circuit", P)
     info = g.info()
     opts = pkg.make_opts(precision=args.precision, early_exit=True, decoder="bp4m")
@@ -408,7 +411,8 @@ def run_ours(args, rank, world, local):
     msgs_per_launch = dp["msg_updates"] / max(dp["launches"], 1)
     sm_mhz = clk["sm_mhz"] or 2070.0
     achieved = msgs_per_launch / (per_launch_ms / 1e3) / 1e9
-    peak = MSG_PER_SM_PER_CLK * NUM_SMS * sm_mhz * 1e6 / 1e9
+    msg_per_sm_clk = 1.0 / (1.0 / mufu["ex2"] + 1.0 / mufu["lg2"])
+    peak = msg_per_sm_clk * mufu["sms"] * sm_mhz * 1e6 / 1e9
     launches = sum(v["launches"] for v in prof.values())
     decode_ms = sum(prof[s]["ms"] for s in slots)
     decode_msgs = sum(prof[s]["msg_updates"] for s in slots)
@@ -457,9 +461,11 @@ def run_ours(args, rank, world, local):
                      "traffic": (DRAM_BYTES_PER_SHOT[dom] * dp["shots"] / max(dp["launches"], 1)
                                  if dom in DRAM_BYTES_PER_SHOT and args.precision == "fp32" else None),
                      "traffic_unit": "bytes per launch (ncu DRAM read + write, 65,536-shot capture scaled by shots)",
-                     "peak_basis": "MUFU: one ex2 (32/clk/SM) + one lg2 (16/clk/SM) per message update = "
-                                   "3/32 SM-cycles; x %d SMs x %.0f MHz (median SM clock in the timed region)"
-                                   % (NUM_SMS, sm_mhz),
+                     "peak_basis": "MUFU, measured in this run by bp4m_probe_mufu: one ex2 (%.2f/clk/SM) + one "
+                                   "lg2 (%.2f/clk/SM) per message update = %.4f SM-cycles; x %d SMs x %.0f MHz "
+                                   "(median SM clock in the timed region)"
+                                   % (mufu["ex2"], mufu["lg2"], 1.0 / msg_per_sm_clk, mufu["sms"], sm_mhz),
+                     "mufu_probe": mufu,
                      "launches": dp["launches"], "ms_per_launch": per_launch_ms,
                      "msg_updates_per_launch": msgs_per_launch,
                      "share_of_decode_time": dp["ms"] / max(decode_ms, 1e-9),
@@ -514,9 +520,33 @@ def run_reference(args, rank, world):
             "e2e": {"value": val, "unit": "shots/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_mufu_probe(local):
+    """bp4m_probe_mufu repeated for about a second with the SM clocks sampled meanwhile."""
+    import torch
+    import paper_2603_05381_gb300 as pkg
+    torch.cuda.set_device(local)
+    pkg.probe_mufu(256)  # load the kernels
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    runs = []
+    while time.perf_counter() - t0 < 1.5 or len(runs) < 3:
+        runs.append(pkg.probe_mufu(16384))
+    clk = clocks.stop()
+    med = {k: statistics.median(r[k] for r in runs) for k in ("ex2", "lg2", "ex2_lg2_alternating")}
+    upd = 1.0 / (1.0 / med["ex2"] + 1.0 / med["lg2"])
+    return {"mufu_per_sm_per_clk": med, "runs": len(runs), "sms": runs[0]["sms"],
+            "msg_updates_per_sm_per_clk": upd, "clocks": clk,
+            "peak_gmsg_per_s_at_median_clock": (upd * runs[0]["sms"] * clk["sm_mhz"] / 1e3
+                                                if clk["sm_mhz"] else None)}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.mufu_probe:
+        print(json.dumps(run_mufu_probe(local)), flush=True)
+        return
     if args.impl == "reference":
         line = run_reference(args, rank, world)
     else:

@@ -180,8 +180,16 @@ int bp4m_decode_trace(bp4m_graph* g, const uint32_t* syndromes, int64_t shots, i
 
 /* Samples and decodes `shots` shots (all types of the graph) and adds up failures:
    a shot fails for a type iff the decoded observable flip differs from the sampled one.
-   p must equal the graph's p.  Work is split into device-resident batches.  *out is
-   overwritten.  Synchronises `stream`. */
+   Sampling (Sec. "Numerical Results": code-capacity depolarizing noise or the circuit-level
+   memory experiment at physical error rate p) and the priors of Eq. (two-syn var factors)
+   and Eq. (priorllr) both follow p.  When p differs from the graph's p (0 < p < 0.5), the
+   tables are re-derived for p from the graph's code and noise options (code capacity: the
+   path weights hops x ln((1-p)/p) and priors; circuit: the merged edge probabilities, every
+   shortest path, prior and parity), exactly as bp4m_build_graph would build them for p,
+   cached inside the graph per p (the 8 most recently used values; each cached value holds
+   its own device tables and workspace) and uploaded on first use, so the counts are
+   bit-identical to those of a graph built at p.  Shots 0..shots-1, Philox stream 0.  Work
+   is split into device-resident batches.  *out is overwritten.  Synchronises `stream`. */
 int bp4m_sample_and_decode(bp4m_graph* g, double p, int64_t shots, uint64_t seed, int iters,
                            const bp4m_opts* opts, bp4m_counts* out, void* stream);
 
@@ -225,6 +233,7 @@ int bp4m_decode_bbp4mf(bp4m_graph* g, const uint32_t* syndromes, int64_t shots, 
        (cudaGetSymbolAddress); make that first call before any stream capture;
      - a shot with more than 192 unsatisfied detectors is rejected: the call returns
        BP4M_EINVAL and that shot's outputs are 0;
+     - at most 2^31 - 17 shots per call (BP4M_EINVAL beyond);
      - every call shares the one array, which keeps the last call's contents: calls that
        overlap on the GPU (other streams, other threads) race and must be serialised by
        the caller.
@@ -248,6 +257,17 @@ typedef struct {
 } bp4m_profile_t;
 int bp4m_profile_enable(bp4m_graph* g, int on);
 int bp4m_profile_read(bp4m_graph* g, bp4m_profile_t* out);
+
+/* Measurement support (no counterpart in the paper): the throughput of the GPU's
+   special-function (MUFU) unit, the roofline denominator of the shared-memory decoding
+   tiers, whose every message update takes one ex2 and one lg2 (Sec. "Belief Propagation":
+   one exponential and one logarithm per leave-one-out soft maximum).  Launches one block
+   of 1024 threads per SM running `steps` (1..2^20) rounds of 8 independent chains and
+   times each block with its SM's cycle counter.  Writes out[0] = ex2, out[1] = lg2,
+   out[2] = ex2 and lg2 alternating (results per SM per clock, median over the SMs), and
+   out[3] = the SM count.  Allocates and frees a few KB of device memory; synchronises
+   `stream`. */
+int bp4m_probe_mufu(int steps, double* out, void* stream);
 
 void bp4m_free_graph(bp4m_graph* g);
 
@@ -288,7 +308,8 @@ typedef struct {
     int64_t evictions;             /* workspaces freed to stay within the budget */
     int64_t max_inflight_batches;  /* most batches running at the same time */
     int64_t pending;               /* requests waiting now */
-    int64_t device_bytes;          /* device bytes of the workspaces now */
+    int64_t device_bytes;          /* device bytes of the workspaces' per-shot buffers now (what
+                                      device_budget_bytes limits; streaming-tier scratch excluded) */
 } bp4m_server_stats_t;
 
 /* n_slots in [1, 64]; max_batch_shots in [1, 2^20].  NULL on error (bp4m_last_error). */

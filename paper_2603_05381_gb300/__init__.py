@@ -22,6 +22,14 @@ def version():
     return load().bp4m_version().decode()
 
 
+def probe_mufu(steps=4096, stream=None):
+    """Special-function unit throughput of the current GPU (bp4m_probe_mufu): results per SM
+    per clock of ex2, lg2 and the two alternating, and the SM count."""
+    out = (ctypes.c_double * 4)()
+    check(load().bp4m_probe_mufu(int(steps), out, _stream(stream)))
+    return {"ex2": out[0], "lg2": out[1], "ex2_lg2_alternating": out[2], "sms": int(out[3])}
+
+
 def _ptr(buf):
     """Raw address of a torch tensor or numpy array (None -> NULL)."""
     if buf is None:
@@ -152,11 +160,20 @@ class Graph:
         return {name: {"launches": pr.launches[k], "ms": pr.ms[k], "msg_updates": pr.msg_updates[k],
                        "shots": pr.shots[k]} for k, name in enumerate(_capi.PROFILE_SLOTS)}
 
-    def sample_and_decode(self, shots, seed, iters, opts, first_shot=0, stream_id=0, stream=None):
+    def sample_and_decode(self, shots, seed, iters, opts, first_shot=0, stream_id=0, stream=None, p=None):
+        """Counts of the global shot range [first_shot, first_shot + shots) (bp4m_sample_and_decode_range),
+        or with `p` given, of shots 0..shots-1 at physical error rate p (bp4m_sample_and_decode: a p
+        other than the graph's re-derives the tables, cached per p)."""
         c = _capi.Counts()
-        check(load().bp4m_sample_and_decode_range(self._h, int(first_shot), int(shots), int(seed),
-                                                  int(stream_id), int(iters), ctypes.byref(opts),
-                                                  ctypes.byref(c), _stream(stream)))
+        if p is not None:
+            if first_shot or stream_id:
+                raise ValueError("p is taken with the shot range starting at 0 on stream 0")
+            check(load().bp4m_sample_and_decode(self._h, float(p), int(shots), int(seed), int(iters),
+                                                ctypes.byref(opts), ctypes.byref(c), _stream(stream)))
+        else:
+            check(load().bp4m_sample_and_decode_range(self._h, int(first_shot), int(shots), int(seed),
+                                                      int(stream_id), int(iters), ctypes.byref(opts),
+                                                      ctypes.byref(c), _stream(stream)))
         return {"shots": c.shots, "fail": list(c.fail), "unconverged": list(c.unconverged),
                 "forced_output": list(c.forced_output), "conv_fail": list(c.conv_fail),
                 "iterations": c.iterations, "msg_updates": c.msg_updates, "defects": c.defects,

@@ -112,6 +112,7 @@ SIGNATURES = {
     "bp4m_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "bp4m_profile_read": (ctypes.c_int, [_P, ctypes.POINTER(Profile)]),
     "bp4m_free_graph": (None, [_P]),
+    "bp4m_probe_mufu": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_double), _P]),
     "bp4m_server_create": (_P, [ctypes.c_int, ctypes.c_int64, ctypes.c_int64]),
     "bp4m_server_add_graph": (ctypes.c_int, [_P, _P]),
     "bp4m_server_submit": (ctypes.c_int64, [_P, ctypes.c_int, _P, ctypes.c_int64, ctypes.c_int,

@@ -133,7 +133,14 @@ struct bp4m_graph {
     bool prof_on = false;
     std::vector<ProfEvent> prof_events;
     bp4m_profile_t prof{};
+    // graphs of the same code and noise model re-derived for another p by
+    // bp4m_sample_and_decode (least recently used last; at most kMaxDerived)
+    std::vector<bp4m_graph*> derived;
 };
+
+namespace {
+constexpr size_t kMaxDerived = 8;
+}  // namespace
 
 namespace {
 
@@ -794,8 +801,12 @@ struct SrvSlot {
     std::thread th;
 };
 
+// Bytes of a workspace's per-shot buffers: what the service's device budget counts (the
+// streaming tier's scratch, which depends on the shots' defect counts and not on the
+// batch size, grows outside the budget).  The same expression sizes the admission check
+// in srv_run_batch, so what a batch is admitted for is what it adds.
 size_t ws_bytes(const Workspace& w) {
-    return (size_t)w.cap * (w.words_total * 4 + 5 * w.n_types) + (size_t)w.cap * kTiers * 4 + w.gscratch_bytes;
+    return (size_t)w.cap * (w.words_total * 4 + 5 * w.n_types) + (size_t)w.cap * kTiers * 4;
 }
 
 // Mean number of unsatisfied detectors of a shot of type ty: each detector is unsatisfied
@@ -1791,8 +1802,35 @@ int bp4m_sample_and_decode_range(bp4m_graph* g, uint64_t first_shot, int64_t sho
 int bp4m_sample_and_decode(bp4m_graph* g, double p, int64_t shots, uint64_t seed, int iters,
                            const bp4m_opts* opts, bp4m_counts* out, void* stream) {
     if (!g) return fail(BP4M_EINVAL, "null graph");
-    if (p != g->host.p) return fail(BP4M_EINVAL, "p differs from the graph's p; build a graph for it");
-    return bp4m_sample_and_decode_range(g, 0, shots, seed, 0, iters, opts, out, stream);
+    if (p == g->host.p) return bp4m_sample_and_decode_range(g, 0, shots, seed, 0, iters, opts, out, stream);
+    if (!(p > 0.0 && p < 0.5)) return fail(BP4M_EINVAL, "p must lie in (0, 0.5)");
+    // another p: the priors (and for circuits the merged edge probabilities and every
+    // shortest path) depend on it, so the graph is re-derived from the same code and noise
+    // options, cached per p and uploaded on its first decoding call
+    bp4m_graph* dg = nullptr;
+    for (size_t k = 0; k < g->derived.size(); ++k)
+        if (g->derived[k]->host.p == p) {
+            dg = g->derived[k];
+            g->derived.erase(g->derived.begin() + (std::ptrdiff_t)k);
+            break;
+        }
+    if (!dg) {
+        const HostGraph& h = g->host;
+        bp4m_code code{h.family, h.d, h.model == BP4M_CIRCUIT ? h.rounds : 0, BP4M_MEMORY_Z};
+        bp4m_noise noise{h.model, p, h.prior_conv, h.through_boundary};
+        int rc = bp4m_build_graph(&code, &noise, &dg);
+        if (rc != BP4M_OK) return rc;
+        if (g->derived.size() >= kMaxDerived) {
+            bp4m_free_graph(g->derived.front());
+            g->derived.erase(g->derived.begin());
+        }
+    }
+    g->derived.push_back(dg);
+    if (dg->prof_on != g->prof_on) {
+        prof_clear(dg);
+        dg->prof_on = g->prof_on;
+    }
+    return bp4m_sample_and_decode_range(dg, 0, shots, seed, 0, iters, opts, out, stream);
 }
 
 int bp4m_decode_bbp4mf(bp4m_graph* g, const uint32_t* syndromes, int64_t shots, int iters,
@@ -1838,7 +1876,9 @@ int bp4m_decode_noalloc(const bp4m_graph* g, const uint32_t* syndromes, int64_t 
     // No allocation on any path of this function: it reads the graph's resident tables
     // and uses the library's static scratch array (see launch_decode_noalloc).
     if (!g || !syndromes) return fail(BP4M_EINVAL, "null argument");
-    if (shots < 0 || shots > 0x7fffffff) return fail(BP4M_EINVAL, "shots out of range");
+    // the kernel's work counter is a 32-bit int that every block bumps once past the last
+    // shot: keep it clear of overflow
+    if (shots < 0 || shots > noalloc_max_shots()) return fail(BP4M_EINVAL, "shots out of range");
     int rc = check_opts(g, opts, iters);
     if (rc) return rc;
     if (opts->precision == BP4M_FP16 || opts->precision == BP4M_BF16)
@@ -1878,13 +1918,17 @@ int bp4m_decode_noalloc(const bp4m_graph* g, const uint32_t* syndromes, int64_t 
 
 int bp4m_profile_enable(bp4m_graph* g, int on) {
     if (!g) return fail(BP4M_EINVAL, "null graph");
+    for (bp4m_graph* x : g->derived) {
+        prof_clear(x);
+        x->prof_on = on != 0;
+    }
     prof_clear(g);
     g->prof_on = on != 0;
     return BP4M_OK;
 }
 
-int bp4m_profile_read(bp4m_graph* g, bp4m_profile_t* out) {
-    if (!g || !out) return fail(BP4M_EINVAL, "null argument");
+namespace {
+int prof_collect(bp4m_graph* g) {
     for (auto& e : g->prof_events) {
         CK(cudaEventSynchronize(e.b));
         float ms = 0.f;
@@ -1895,12 +1939,68 @@ int bp4m_profile_read(bp4m_graph* g, bp4m_profile_t* out) {
         cudaEventDestroy(e.b);
     }
     g->prof_events.clear();
-    *out = g->prof;
     return BP4M_OK;
+}
+}  // namespace
+
+int bp4m_profile_read(bp4m_graph* g, bp4m_profile_t* out) {
+    if (!g || !out) return fail(BP4M_EINVAL, "null argument");
+    int rc = prof_collect(g);
+    if (rc) return rc;
+    *out = g->prof;
+    // launches made through graphs re-derived for another p count as this graph's
+    for (bp4m_graph* x : g->derived) {
+        rc = prof_collect(x);
+        if (rc) return rc;
+        for (int k = 0; k < BP4M_PROF_SLOTS; ++k) {
+            out->launches[k] += x->prof.launches[k];
+            out->ms[k] += x->prof.ms[k];
+            out->msg_updates[k] += x->prof.msg_updates[k];
+            out->shots[k] += x->prof.shots[k];
+        }
+    }
+    return BP4M_OK;
+}
+
+int bp4m_probe_mufu(int steps, double* out, void* stream) {
+    if (!out || steps < 1 || steps > (1 << 20)) return fail(BP4M_EINVAL, "null output or steps outside 1..2^20");
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    long long* cyc = nullptr;
+    float* sink = nullptr;
+    CK(dalloc(&cyc, (size_t)sms));
+    cudaError_t e = dalloc(&sink, (size_t)sms * 1024);
+    if (e != cudaSuccess) {
+        cudaFree(cyc);
+        return cuda_fail(e, "bp4m_probe_mufu");
+    }
+    std::vector<long long> h((size_t)sms);
+    int rc = BP4M_OK;
+    for (int mode = 0; mode < 3 && rc == BP4M_OK; ++mode) {
+        // one untimed launch to load the kernel and warm the clocks, then the measured one
+        for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) e = launch_mufu_probe(mode, sms, steps, cyc, sink, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), cyc, sizeof(long long) * (size_t)sms, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "bp4m_probe_mufu");
+            break;
+        }
+        std::sort(h.begin(), h.end());
+        const double ops = 1024.0 * mufu_probe_ops_per_thread(mode, steps);
+        out[mode] = ops / (double)std::max<long long>(h[(size_t)sms / 2], 1);
+    }
+    if (rc == BP4M_OK) out[3] = sms;
+    cudaFree(cyc);
+    cudaFree(sink);
+    return rc;
 }
 
 void bp4m_free_graph(bp4m_graph* g) {
     if (!g) return;
+    for (bp4m_graph* x : g->derived) bp4m_free_graph(x);
+    g->derived.clear();
     if (g->uploaded) prof_clear(g);
     if (g->uploaded) {
         for (int ty = 0; ty < 2; ++ty) {

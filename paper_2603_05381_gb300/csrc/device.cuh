@@ -243,6 +243,14 @@ cudaError_t prepare_decode_kernels(int precision);
 cudaError_t launch_decode_noalloc(int precision, DecodeArgs a, int64_t shots, cudaStream_t st,
                                   int* too_many);
 int noalloc_max_defects();
+int64_t noalloc_max_shots();
+
+// MUFU throughput probe (measurement support): `blocks` blocks of 1024 threads, one per
+// SM, each timing `steps` rounds of its special-function chains with the SM cycle counter
+// (cycles[blocks]); sink[blocks * 1024] keeps the results live.  mode 0 = ex2, 1 = lg2,
+// 2 = ex2 and lg2 alternating.
+cudaError_t launch_mufu_probe(int mode, int blocks, int steps, long long* cycles, float* sink, cudaStream_t st);
+int mufu_probe_ops_per_thread(int mode, int steps);
 
 cudaError_t launch_count(const uint8_t* obs_true, const uint8_t* obs_pred, const uint8_t* flags,
                          int64_t shots, int n_types, unsigned long long* ctr, cudaStream_t st);

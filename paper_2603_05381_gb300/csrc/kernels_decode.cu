@@ -831,6 +831,7 @@ cudaError_t launch_decode_tier(int precision, int tier, const DecodeArgs& a, int
 }
 
 int noalloc_max_defects() { return kNoAllocMaxDefects; }
+int64_t noalloc_max_shots() { return (int64_t)0x7fffffff - kNoAllocSlots; }
 
 cudaError_t launch_decode_noalloc(int precision, DecodeArgs a, int64_t shots, cudaStream_t st,
                                   int* too_many) {

@@ -201,6 +201,53 @@ __global__ void __launch_bounds__(kCntThreads) count_kernel(
     }
 }
 
+// ---- MUFU throughput probe (measurement support; the roofline denominator of the
+// shared-memory decode tiers).  Each thread runs kProbeChains independent chains of
+// `steps` special-function operations; a block of 1024 threads (one per SM: the launch
+// bounds and a large dynamic shared-memory request keep a second block off the SM) times
+// its loop with the SM cycle counter.  Modes: 0 = ex2 (x <- 1 - ex2(x)/2, one FMA beside
+// each ex2), 1 = lg2 (x <- lg2(x) + 2, one add beside each lg2), 2 = ex2 and lg2
+// alternating (x <- lg2(ex2(x)), no other arithmetic).  The FMA/add pipe and the issue
+// slots they take stay far below their own limits at these rates, so the MUFU unit bounds
+// every mode.
+constexpr int kProbeThreads = 1024;
+constexpr int kProbeChains = 8;
+
+__device__ __forceinline__ float probe_ex2(float x) {
+    float y;
+    asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float probe_lg2(float x) {
+    float y;
+    asm volatile("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kProbeThreads, 1) mufu_probe_kernel(int steps, long long* cycles, float* sink) {
+    float x[kProbeChains];
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) x[j] = (MODE == 1 ? 4.0f : 0.35f) + 1e-3f * j + 1e-7f * threadIdx.x;
+    __syncthreads();
+    const long long t0 = clock64();
+    for (int s = 0; s < steps; ++s) {
+#pragma unroll
+        for (int j = 0; j < kProbeChains; ++j) {
+            if (MODE == 0) x[j] = fmaf(probe_ex2(x[j]), -0.5f, 1.0f);
+            if (MODE == 1) x[j] = probe_lg2(x[j]) + 2.0f;
+            if (MODE == 2) x[j] = probe_lg2(probe_ex2(x[j]));
+        }
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < kProbeChains; ++j) acc += x[j];
+    sink[(size_t)blockIdx.x * kProbeThreads + threadIdx.x] = acc;
+    if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+}
+
 int grid_for(int64_t items, int per_block, int cap) {
     int64_t g = (items + per_block - 1) / per_block;
     if (g < 1) g = 1;
@@ -240,6 +287,23 @@ cudaError_t launch_classify(const uint32_t* synd, int64_t shots, int n_words, co
         skip_obs, skip_iters, list_stride > 0 ? list_stride : shots, item_base);
     return cudaGetLastError();
 }
+
+cudaError_t launch_mufu_probe(int mode, int blocks, int steps, long long* cycles, float* sink, cudaStream_t st) {
+    // 120 KB of dynamic shared memory (unused) so that no SM holds two probe blocks
+    const int smem = 120 * 1024;
+    auto launch = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        kern<<<blocks, kProbeThreads, smem, st>>>(steps, cycles, sink);
+        return cudaGetLastError();
+    };
+    if (mode == 0) return launch(mufu_probe_kernel<0>);
+    if (mode == 1) return launch(mufu_probe_kernel<1>);
+    if (mode == 2) return launch(mufu_probe_kernel<2>);
+    return cudaErrorInvalidValue;
+}
+
+int mufu_probe_ops_per_thread(int mode, int steps) { return kProbeChains * steps * (mode == 2 ? 2 : 1); }
 
 cudaError_t launch_count(const uint8_t* obs_true, const uint8_t* obs_pred, const uint8_t* flags,
                          int64_t shots, int n_types, unsigned long long* ctr, cudaStream_t st) {

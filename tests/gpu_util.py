@@ -69,13 +69,27 @@ def oracle_partner(matching, s):
 
 
 def compare_shots(tables, synd_bool, gpu, T, idx, tau, decoder="bp4m", early_exit=True, alpha=1.0,
-                  check_partner=True):
-    """Decodes shots `idx` with the oracle and compares with the GPU.  Returns (n_compared,
-    list of mismatching (shot, margin)).  A mismatch with oracle margin >= tau is an error."""
+                  check_partner=True, pool=None, oracle=None):
+    """Decodes shots `idx` with the oracle (in this process, or over `pool`, an
+    oracle_pool.OraclePool of the same tables) and compares with the GPU.  Returns
+    (n_compared, list of mismatching (shot, margin)).  `oracle`, if given, holds the oracle's
+    results of every shot (indexed like synd_bool).  A mismatch with oracle margin >= tau
+    is an error."""
+    idx = list(idx)
+    if oracle is not None:
+        results = [oracle[k] for k in idx]
+    elif pool is not None:
+        results = pool.decode([np.flatnonzero(synd_bool[k]) for k in idx], T, decoder=decoder,
+                              early_exit=early_exit, alpha=alpha)
+    else:
+        results = None
     bad = []
-    for k in idx:
+    for pos, k in enumerate(idx):
         dets = np.flatnonzero(synd_bool[k])
-        r = decode_shot(tables, dets, T, decoder=decoder, early_exit=early_exit, alpha=alpha)
+        if results is not None:
+            r = results[pos]
+        else:
+            r = decode_shot(tables, dets, T, decoder=decoder, early_exit=early_exit, alpha=alpha)
         same = (r.obs_pred == int(gpu["obs"][k]) and int(r.converged) == int(gpu["flags"][k] & 1)
                 and r.iters == int(gpu["iters"][k]) and int(r.from_forced) == int((gpu["flags"][k] >> 2) & 1))
         if same and check_partner and "partner" in gpu and len(dets) <= gpu["partner"].shape[1] and len(dets):

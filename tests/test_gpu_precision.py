@@ -1,10 +1,11 @@
 """16-bit message storage (FP16 or BF16 messages; FP32 priors and arithmetic) against the
 FP32 path on the same shots and against the FP64 oracle.
 
-The bar for reduced precision is statistical: the logical error rate on the benchmark's
-d = 13 circuit workload must lie within one Monte Carlo standard error of the FP32 rate on
-the same shots.  The posterior LLRs after T iterations are compared with the oracle's
-(error relative to |l| + 1, reported per format), and so is the per-shot output."""
+The bar for reduced precision: the logical error rate on the benchmark's d = 13 circuit
+workload within one Monte Carlo standard error of the FP32 rate on the same shots, and hard
+decisions (predicted flips) identical to FP32 and to the oracle on at least 99.99% of shots.
+The posterior LLRs after T iterations are compared with the oracle's (error relative to
+|l| + 1, reported per format)."""
 import numpy as np
 import pytest
 
@@ -15,6 +16,7 @@ from oracle.graph import circuit_tables
 from oracle.sampler import unpack_syndromes
 
 from gpu_util import compare_shots, gpu_decode, gpu_sample, torch_cuda
+from oracle_pool import OraclePool
 
 pytestmark = pytest.mark.gpu
 
@@ -40,30 +42,56 @@ def _decode(g, synd, T, prec):
     return pred.cpu().numpy(), its.cpu().numpy()
 
 
-# minimum fraction of shots whose output equals the FP32 output (measured on a GB300:
-# 0.9998 for FP16, 0.9979 for BF16)
-AGREE = {"fp16": 0.999, "bf16": 0.99}
-# largest fraction of the oracle comparison's shots allowed to differ (measured: 1 and 2 of
-# 400)
-ORACLE_DIFF = {"fp16": 0.01, "bf16": 0.02}
+# The bar for reduced precision: hard decisions (each shot's predicted observable flip)
+# identical to the FP32 path and to the FP64 oracle on at least 99.99% of shots, and the
+# logical error rate within one Monte Carlo standard error of FP32.  A format that misses
+# the decision bar is marked as a known miss with the figure measured on a GB300.
+AGREE_BAR = 0.9999
+KNOWN_MISS_FP32 = {}
+KNOWN_MISS_ORACLE = {}
+
+
+def _maybe_known_miss(prec, table):
+    if prec in table:
+        return pytest.param(prec, marks=pytest.mark.xfail(strict=False, reason=table[prec]))
+    return prec
+
+
+_d13 = {}
+
+
+def _d13_outputs(prec):
+    """Outputs of FP32 and `prec` on 2^18 shots of the benchmark's d = 13 circuit workload."""
+    if "g" not in _d13:
+        g = pkg.Graph(13, "circuit", 0.005)
+        n, T = 1 << 18, 50
+        (synd,), obs = gpu_sample(g, 0, n, seed=11)
+        _d13.update(g=g, synd=synd, obs=obs[0].cpu().numpy(), T=T, n=n)
+        _d13["fp32"] = _decode(g, synd, T, "fp32")[0]
+    if prec not in _d13:
+        _d13[prec] = _decode(_d13["g"], _d13["synd"], _d13["T"], prec)[0]
+    return _d13["obs"], _d13["fp32"], _d13[prec]
 
 
 @pytest.mark.parametrize("prec", ["fp16", "bf16"])
 def test_reduced_precision_ler_within_one_standard_error(prec):
-    g = pkg.Graph(13, "circuit", 0.005)
-    n, T = 1 << 18, 50
-    (synd,), obs = gpu_sample(g, 0, n, seed=11)
-    obs = obs[0].cpu().numpy()
-    p32, _ = _decode(g, synd, T, "fp32")
-    p16, _ = _decode(g, synd, T, prec)
+    obs, p32, p16 = _d13_outputs(prec)
+    n = obs.shape[0]
     ler32 = float((p32 != obs).mean())
     ler16 = float((p16 != obs).mean())
     sigma = np.sqrt(ler32 * (1 - ler32) / n)
-    agree = float((p16 == p32).mean())
-    print("%s: LER %.5f vs FP32 %.5f (sigma %.5f, diff %.2f sigma), outputs equal on %.4f of shots"
-          % (prec, ler16, ler32, sigma, (ler16 - ler32) / sigma, agree))
+    print("%s: LER %.5f vs FP32 %.5f (sigma %.5f, diff %.2f sigma)" % (prec, ler16, ler32, sigma,
+                                                                      (ler16 - ler32) / sigma))
     assert abs(ler16 - ler32) <= sigma
-    assert agree >= AGREE[prec]
+
+
+@pytest.mark.parametrize("prec", [_maybe_known_miss(p, KNOWN_MISS_FP32) for p in ("fp16", "bf16")])
+def test_reduced_precision_decisions_agree_with_fp32(prec):
+    obs, p32, p16 = _d13_outputs(prec)
+    agree = float((p16 == p32).mean())
+    print("%s: outputs equal to FP32 on %.5f of %d shots (%d differ)" % (prec, agree, p32.shape[0],
+                                                                        int((p16 != p32).sum())))
+    assert agree >= AGREE_BAR
 
 
 # bound on max |lambda - lambda_oracle| / (|l| + 1) after T iterations (measured: 0.0014
@@ -95,16 +123,24 @@ def test_reduced_precision_posteriors_vs_oracle(prec):
     assert worst < LAM_TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("prec", [_maybe_known_miss(p, KNOWN_MISS_ORACLE) for p in ("fp16", "bf16")])
 def test_reduced_precision_outputs_vs_oracle(prec):
+    # 10^4 shots of the d = 5 circuit at p = 0.008 against the oracle over every host core:
+    # the predicted flip must agree on at least 99.99% of them; convergence, iteration count
+    # and matching are reported
     g, og, ot = _pair(5, 0.008)
-    n, T = 400, 30
+    n, T = 10000, 30
     (synd,), _ = gpu_sample(g, 1000, n, seed=5)
     res = gpu_decode(g, synd, T, pkg.make_opts(precision=prec, early_exit=True), s_cap=64)
     sb = unpack_syndromes(synd.cpu().numpy().view(np.uint32), og.n_det)
-    cnt, bad = compare_shots(ot, sb, res, T, range(n), 1e9)
-    print("%s d5: %d/%d shots differ from the FP64 oracle (output, convergence, iterations)" % (prec, len(bad), cnt))
-    assert len(bad) <= cnt * ORACLE_DIFF[prec]
+    with OraclePool(ot) as pool:
+        ref = pool.decode([np.flatnonzero(r) for r in sb], T)
+    obs_ref = np.array([r.obs_pred for r in ref])
+    same_obs = float((obs_ref == res["obs"]).mean())
+    cnt, bad = compare_shots(ot, sb, res, T, range(n), 1e9, oracle=ref)
+    print("%s d5: predicted flip equal to the FP64 oracle on %.5f of %d shots; %d shots differ in "
+          "(flip, convergence, iterations, output source, matching)" % (prec, same_obs, n, len(bad)))
+    assert same_obs >= AGREE_BAR
 
 
 def test_reduced_precision_rejected_where_unsupported():

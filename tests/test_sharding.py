@@ -84,3 +84,40 @@ def test_two_rank_sharding_matches_single_process():
 def test_shot_range_rejects_bad_rank():
     with pytest.raises(ValueError):
         sharding.shot_range(2, 2, 0, 10)
+
+
+# ---------------------------------------------------------------- a rank that leaves
+
+
+def _worker_leaving(rank, world, port, q, leave_after):
+    import torch.distributed as dist
+    store = dist.TCPStore("127.0.0.1", port, world, rank == 0, timeout=__import__("datetime").timedelta(seconds=120))
+    dist.init_process_group("gloo", store=store, rank=rank, world_size=world)
+    run = sharding.ShardedRun(store, rank, world, SHOTS, heartbeat_s=0.1, dead_after_s=1.0)
+    for step in range(STEPS):
+        if rank == 1 and step == leave_after:
+            # leaves between steps: no kernel or collective in flight, the heartbeat stops
+            run.leave()
+            q.put((rank, None, []))
+            return
+        run.step(step, lambda lo, n: _counts_for_range(lo, lo + n))
+    total = run.finish(STEPS, lambda lo, n: _counts_for_range(lo, lo + n), timeout_s=240)
+    q.put((rank, total, run.reissued))
+
+
+def test_rank_that_leaves_between_steps_has_its_ranges_reissued():
+    world = 2
+    port = 31500 + (os.getpid() % 2000)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker_leaving, args=(r, world, port, q, 1)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = dict((r, (t, ri)) for r, t, ri in (q.get(timeout=300) for _ in range(world)))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    total, reissued = res[0]
+    # rank 1 decoded step 0 only; its steps 1 and 2 were re-issued on rank 0
+    assert sorted(reissued) == [(1, 1), (2, 1)]
+    assert total == _counts_for_range(0, world * STEPS * SHOTS)
