@@ -78,6 +78,13 @@ def parse():
     # only measure the special-function unit (the shared-memory tiers' roofline
     # denominator) with the SM clocks sampled meanwhile, print it and exit
     ap.add_argument("--mufu-probe", action="store_true")
+    # threshold sweeps (code-capacity and circuit-level grids of the paper's experiments):
+    # one JSON line per (d, p) point instead of the benchmark line
+    ap.add_argument("--sweep", choices=["code_capacity", "circuit"], default=None)
+    ap.add_argument("--sweep-shots", type=int, default=1000000)
+    ap.add_argument("--sweep-state", default=None, help="JSON-lines checkpoint (resumed if present)")
+    ap.add_argument("--sweep-d", default=None)
+    ap.add_argument("--sweep-p", default=None)
     return ap.parse_args()
 
 
@@ -541,11 +548,47 @@ def run_mufu_probe(local):
                                                 if clk["sm_mhz"] else None)}
 
 
+def measured_hbm_gbs():
+    """The machine's measured copy bandwidth (MEASURED_PEAKS.json), else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_sweep(args, local):
+    """Every point of a sweep through the library, with per-point statistics and the
+    dominant tier's roofline fraction (special-function roof measured in this run; HBM
+    roof from the measured copy bandwidth)."""
+    import torch
+    import paper_2603_05381_gb300 as pkg
+    from paper_2603_05381_gb300 import sweep as sw
+    torch.cuda.set_device(local)
+    probe = run_mufu_probe(local)
+    hbm, hbm_kind = measured_hbm_gbs()
+    sm_mhz = probe["clocks"]["sm_mhz"] or 2070.0
+    peak = {"hbm_gbs": hbm, "mufu_gmsg": probe["msg_updates_per_sm_per_clk"] * probe["sms"] * sm_mhz / 1e3}
+    ds = tuple(int(x) for x in args.sweep_d.split(",")) if args.sweep_d else None
+    ps = tuple(float(x) for x in args.sweep_p.split(",")) if args.sweep_p else None
+    pts = sw.config_points(args.sweep, ds, ps)
+    print(json.dumps({"sweep": args.sweep, "points": len(pts), "shots_per_point": args.sweep_shots,
+                      "peaks": dict(peak, hbm_kind=hbm_kind, sm_mhz=sm_mhz), "mufu_probe": probe}), flush=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    sw.sweep(pts, args.sweep_shots, state_path=args.sweep_state, seed=SEED, profile=True, peak=peak, log=sys.stdout)
+    print(json.dumps({"sweep_done": args.sweep, "clocks": clocks.stop()}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.mufu_probe:
         print(json.dumps(run_mufu_probe(local)), flush=True)
+        return
+    if args.sweep:
+        if rank == 0:
+            run_sweep(args, local)
         return
     if args.impl == "reference":
         line = run_reference(args, rank, world)

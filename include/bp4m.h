@@ -203,11 +203,14 @@ int bp4m_sample_and_decode_range(bp4m_graph* g, uint64_t first_shot, int64_t sho
 /* B-BP4MF (Sec. "Belief-BP4MF (B-BP4MF)" and Sec. "Correlated decoding") on code-capacity
    graphs.  First stage: quaternary BP on the Tanner graph with `iters` iterations and the
    graph's p as the depolarizing prior; a shot whose hard decision reproduces its syndrome
-   takes that decision.  Otherwise, per type, every data qubit's edge of the decoding graph is
-   weighted max(ln((1-P)/P), 2^-20) with P its posterior of an error component of that type
-   (the floor keeps shortest paths defined when P >= 1/2, a case the paper does not treat),
-   Dijkstra from every unsatisfied check yields the shot's priors, and BP4MF (alpha from
-   opts) runs for `iters` iterations.  At most 160 (FP32) or 112 (FP64) unsatisfied checks
+   takes that decision.  Otherwise, per type, every data qubit is an edge of the decoding
+   graph with P its posterior of an error component of that type.  An edge with P > 1/2
+   (negative weight, a case the paper does not treat) is taken as present, as matching
+   decoders with negative weights do: its endpoints flip in the shot's syndrome, its
+   observable bit is added to the output, and it weighs as its complement.  Every edge then
+   weighs max(|ln((1-P)/P)|, 2^-20), Dijkstra from every unsatisfied check of the flipped
+   syndrome yields the shot's priors, and BP4MF (alpha from opts) runs for `iters`
+   iterations.  At most 160 (FP32) or 112 (FP64) unsatisfied checks
    of a type per shot (BP4M_EUNSUPPORTED beyond).  syndromes: uint32 [2][shots][n_words] (type 0 then type 1, the layout of
    bp4m_sample); outputs obs_pred and flags (bit0 converged, bit3 first stage): uint8
    [2][shots]; flags may be NULL.  Host or device buffers.  Synchronises `stream`. */

@@ -9,8 +9,19 @@ every data qubit is an edge of G_D between its one or two checks (one check: to 
 boundary), with weight ln((1 - P_e)/P_e) where P_e is the posterior probability that the
 qubit carries an error component detected by that check type; Dijkstra from every
 unsatisfied check gives the shot's pair and boundary weights, hence its priors
-(Eq. two-syn var factors with the reweighted w), and BP4MF runs on them.  Edge weights are
-floored at MIN_WEIGHT (posteriors >= 1/2; see below).
+(Eq. two-syn var factors with the reweighted w), and BP4MF runs on them.
+
+Posteriors above one half.  The paper does not say how an edge whose posterior P exceeds
+1/2 enters Dijkstra's algorithm (its weight ln((1-P)/P) would be negative, and an undirected
+graph with a negative edge has no shortest paths).  The reading here is the one of
+matching decoders with negative weights (Belief-matching, which Sec. "Correlated decoding"
+emulates): such an edge is taken as present.  Its endpoints' syndrome bits are flipped, its
+observable bit goes into a base parity that is added to the decoded parity, and it enters
+the graph with the complementary probability 1 - P, i.e. weight |ln((1-P)/P)|.  This is an
+exact change of variables of the edge error model (the error E has the probability of
+E + {e} under P_e -> 1 - P_e, and the syndrome of E is that of E + {e} plus the edge's
+endpoints), so it moves no probability mass.  Weights are still floored at MIN_WEIGHT,
+which now only acts at P = 1/2 exactly.
 
 Quaternary BP (the paper cites it without restating it; this is the standard form with
 one scalar message per Tanner edge):
@@ -38,10 +49,8 @@ PAULIS = ("I", "X", "Y", "Z")
 # anticommutation of E with an X-type / Z-type check
 ANTI_X = np.array([0, 0, 1, 1])  # I, X, Y, Z vs X-check: Y, Z anticommute
 ANTI_Z = np.array([0, 1, 1, 0])  # vs Z-check: X, Y anticommute
-# Smallest reweighted edge weight.  A posterior at or above one half gives ln((1-P)/P) <= 0,
-# and on an undirected graph a non-positive edge leaves no minimum-weight path (a negative
-# edge can be walked back and forth); the paper does not treat this case, so such weights
-# are raised to 2^-20 (the path then costs almost nothing and its prior is large but finite).
+# Smallest reweighted edge weight: a posterior of exactly one half gives weight 0, which
+# would make the pair prior infinite; the floor keeps it large but finite.
 MIN_WEIGHT = 2.0 ** -20
 
 
@@ -52,10 +61,16 @@ def tanner(code):
     return out
 
 
-def qbp(checks, n, syndrome, p, T, stop=True):
+def qbp(checks, n, syndrome, p, T, stop=True, margin=None):
     """Quaternary BP.  `checks` = [(type, qubits)], `syndrome` = bits per check.
     Returns (posterior [n, 4], decision [n] of Pauli indices, converged, iterations); with
-    stop=False all T iterations run (used by the exactness checks)."""
+    stop=False all T iterations run (used by the exactness checks).  `margin`, a list,
+    receives per executed iteration the smallest relative gap (q1 - q2) / q1 between a
+    qubit's two largest posteriors that can decide the outcome: any gap of an iteration
+    whose decision reproduces the syndrome; for an unconverged iteration, whose only
+    outcome is its convergence status, at least bp.ROBUST_AT when its mismatched checks
+    outnumber 4 per qubit with a gap below bp.ROBUST_AT (one qubit's decision changes at
+    most 4 checks)."""
     prior = np.array([1.0 - p, p / 3.0, p / 3.0, p / 3.0])
     anti = [ANTI_X if ty == "X" else ANTI_Z for ty, _ in checks]
     edges = [(c, v) for c, (_, qs) in enumerate(checks) for v in qs]
@@ -65,6 +80,7 @@ def qbp(checks, n, syndrome, p, T, stop=True):
         by_qubit[v].append(c)
     post = np.tile(prior, (n, 1))
     dec = np.zeros(n, dtype=int)
+    gaps = np.zeros(n)
     conv = False
     it = 0
     for it in range(1, T + 1):
@@ -90,7 +106,15 @@ def qbp(checks, n, syndrome, p, T, stop=True):
                 q = q * np.exp(-anti[c] * delta[(c, v)])
             post[v] = q / q.sum()
             dec[v] = int(np.argmax(q))
+            if margin is not None:
+                top = np.sort(q)[::-1]
+                gaps[v] = (top[0] - top[1]) / top[0]
         synd = np.array([int(anti[c][dec[qs]].sum() % 2) for c, (_, qs) in enumerate(checks)])
+        if margin is not None:
+            mismatched = int((synd != np.asarray(syndrome, dtype=int)).sum())
+            near = int((gaps < bp.ROBUST_AT).sum())
+            g = float(gaps.min())
+            margin.append(g if (mismatched == 0 or mismatched <= 4 * near) else max(g, bp.ROBUST_AT))
         if np.array_equal(synd, np.asarray(syndrome, dtype=int)):
             conv = True
             if stop:
@@ -98,14 +122,38 @@ def qbp(checks, n, syndrome, p, T, stop=True):
     return post, dec, conv, it
 
 
+def flip_likely_edges(g, edge_prob, synd):
+    """Takes every edge with probability above one half as present: returns the syndrome
+    with their endpoints flipped (bool [n_det]), the XOR of their observable bits, and
+    the number of flipped edges."""
+    out = np.array(synd, dtype=bool).copy()
+    base = 0
+    n = 0
+    for e, (u, v, ob, _) in enumerate(g.edges):
+        if float(edge_prob[e]) > 0.5:
+            out[u] ^= True
+            if v < g.n_det:
+                out[v] ^= True
+            base ^= int(ob)
+            n += 1
+    return out, base, n
+
+
+def edge_weight(prob):
+    """|ln((1-P)/P)| of an edge (its complement when P > 1/2), floored at MIN_WEIGHT."""
+    pe = min(max(float(prob), 1e-300), 1.0 - 1e-16)
+    if pe > 0.5:
+        pe = 1.0 - pe
+    return max(math.log((1.0 - pe) / pe), MIN_WEIGHT)
+
+
 def reweighted_tables(g, edge_prob, dets, through_boundary=False):
     """Shot priors from per-edge error probabilities: W, parity and l over the shot's
     unsatisfied detectors `dets` (W_ij for i < j from the search rooted at the smaller
-    index, diagonal = boundary), same Dijkstra conventions as graph.py."""
-    weights = []
-    for e, (u, v, ob, _) in enumerate(g.edges):
-        pe = min(max(float(edge_prob[e]), 1e-300), 1.0 - 1e-16)
-        weights.append(max(math.log((1.0 - pe) / pe), MIN_WEIGHT))
+    index, diagonal = boundary), same Dijkstra conventions as graph.py.  Edge weights are
+    edge_weight(P) (edges above one half must already have been flipped out of the
+    syndrome by flip_likely_edges)."""
+    weights = [edge_weight(edge_prob[e]) for e in range(len(g.edges))]
     adj = adjacency(g, weights)
     s = len(dets)
     W = np.full((s, s), np.inf)
@@ -126,8 +174,13 @@ def bbp4mf_shot(code, graphs, synd_x_checks, synd_z_checks, p, T_q, T_bp, alpha=
     predicted observable flips and whether the first stage converged."""
     checks = tanner(code)
     syndrome = list(synd_x_checks) + list(synd_z_checks)
-    post, dec, conv, it_q = qbp(checks, code.n, syndrome, p, T_q)
-    out = {"qbp_converged": conv, "qbp_iters": it_q}
+    gaps = []
+    post, dec, conv, it_q = qbp(checks, code.n, syndrome, p, T_q, margin=gaps)
+    # decision margin: first-stage argmax gaps, the distance of every edge's posterior from
+    # the flip threshold 1/2, and the second stage's BP4MF margin
+    out = {"qbp_converged": conv, "qbp_iters": it_q, "margin_qbp": min(gaps) if gaps else math.inf,
+           "margin_flip": math.inf, "margin_bp": math.inf}
+    out["margin"] = out["margin_qbp"]
     if conv:
         ex = (dec == 1) | (dec == 2)   # X component
         ez = (dec == 2) | (dec == 3)   # Z component
@@ -138,17 +191,23 @@ def bbp4mf_shot(code, graphs, synd_x_checks, synd_z_checks, p, T_q, T_bp, alpha=
         g = graphs[kind]
         comp = post[:, 1] + post[:, 2] if kind == "X" else post[:, 2] + post[:, 3]
         edge_prob = [comp[q] for q in g.unit_of_edge]
-        dets = np.flatnonzero(np.asarray(synd, dtype=bool))
+        out["margin_flip"] = min(out["margin_flip"], min(abs(float(x) - 0.5) for x in edge_prob))
+        out["margin"] = min(out["margin"], out["margin_flip"])
+        flipped, base, n_flip = flip_likely_edges(g, edge_prob, synd)
+        out[kind + "_flipped"] = n_flip
+        dets = np.flatnonzero(flipped)
         if len(dets) == 0:
-            out[kind] = 0
+            out[kind] = base
             continue
         W, P, L = reweighted_tables(g, edge_prob, dets)
         r = bp4mf(L, W, T_bp, alpha=alpha)
-        par = 0
+        par = base
         for i, j in r.matching:
             par ^= int(P[i, j])
         out[kind] = par
         out[kind + "_result"] = r
+        out["margin_bp"] = min(out["margin_bp"], r.margin)
+        out["margin"] = min(out["margin"], r.margin)
     return out
 
 

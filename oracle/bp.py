@@ -134,6 +134,66 @@ def forced_convergence(lam, valid=None):
     return picks
 
 
+# Perturbation size up to which decision_margin and the first-stage margin of B-BP4MF check
+# that a decision cannot change: at least the largest tolerance the tests use (1e-2).
+ROBUST_AT = 0.05
+
+
+def greedy_margin(lam, valid=None):
+    """Smallest posterior gap that decides forced_convergence's greedy matching.
+
+    Processing two variables that share no endpoint in the other order gives the same
+    matching, so the result can change under a perturbation of the posteriors only through
+    an accepted variable v and a variable w that shares an endpoint with v and is still
+    available (both endpoints unmatched) when v is accepted: the margin is the smallest
+    lambda_v - lambda_w over such pairs (inf if there are none)."""
+    s = lam.shape[0]
+    if valid is None:
+        valid = full_valid(s)
+    cand = [(-float(lam[i, j]), i, j) for i in range(s) for j in range(i, s) if valid[i, j]]
+    cand.sort()
+    matched = [False] * s
+    margin = math.inf
+    for negl, i, j in cand:
+        if matched[i] or matched[j]:
+            continue
+        best = -math.inf
+        for a in {i, j}:
+            for k in range(s):
+                if matched[k] or not valid[min(a, k), max(a, k)]:
+                    continue
+                if (min(a, k), max(a, k)) == (i, j):
+                    continue
+                best = max(best, float(lam[min(a, k), max(a, k)]))
+        if best > -math.inf:
+            margin = min(margin, -negl - best)
+        matched[i] = True
+        matched[j] = True
+    return margin
+
+
+def decision_margin(lam, valid=None):
+    """Smallest |lambda| that can decide one iteration's marginalization outcome.
+
+    A converged iteration outputs its kept set, so every sign counts: min |lambda|.  An
+    unconverged one only contributes its convergence status, which a sign change moves by
+    at most two rows; if more rows violate the exactly-one rule than twice the number of
+    posteriors within ROBUST_AT of zero, no perturbation below ROBUST_AT can make it
+    converge, and the margin is at least ROBUST_AT."""
+    s = lam.shape[0]
+    if valid is None:
+        valid = full_valid(s)
+    iu = np.triu_indices(s)
+    vals = np.abs(lam[iu])[valid[iu]]
+    m = float(np.min(vals)) if vals.size else math.inf
+    V, conv = decide(lam)
+    if conv:
+        return m
+    viol = int(np.sum(V.sum(axis=1) != 1))
+    near = int(np.sum(vals < ROBUST_AT))
+    return max(m, ROBUST_AT) if viol > 2 * near else m
+
+
 def order_margin(lam):
     """Smallest gap between two different posteriors of the upper triangle (inf if < 2)."""
     s = lam.shape[0]

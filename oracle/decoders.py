@@ -68,7 +68,7 @@ def bp4m(L, W, T, early_exit=True, alpha=1.0, keep_hist=False):
         if keep_hist:
             hist.append(lam.copy())
         r.msg_updates += s * s
-        r.margin = min(r.margin, float(np.min(np.abs(lam[np.triu_indices(s)]))))
+        r.margin = min(r.margin, bp.decision_margin(lam))
         V, conv = bp.decide(lam)
         r.iters = t
         if conv:
@@ -87,7 +87,7 @@ def bp4m(L, W, T, early_exit=True, alpha=1.0, keep_hist=False):
         r.weight, r.matching = best
         return r
     r.fallback = True
-    r.margin = min(r.margin, bp.order_margin(lam))
+    r.margin = min(r.margin, bp.greedy_margin(lam))
     forced = bp.forced_convergence(lam)
     wf = candidate_weight(W, forced)
     if best is not None and best[0] <= wf:
@@ -113,13 +113,13 @@ def bp4mf(L, W, T, alpha=1.0, keep_hist=False):
         if keep_hist:
             hist.append(lam.copy())
         r.msg_updates += s * s
-        r.margin = min(r.margin, float(np.min(np.abs(lam[np.triu_indices(s)]))))
+        r.margin = min(r.margin, bp.decision_margin(lam))
         V, conv = bp.decide(lam)
         if conv:
             any_conv = True
             match, forced = bp.matching_from(V), False
         else:
-            r.margin = min(r.margin, bp.order_margin(lam))
+            r.margin = min(r.margin, bp.greedy_margin(lam))
             match, forced = bp.forced_convergence(lam), True
             r.fallback = True
         w = candidate_weight(W, match)

@@ -101,6 +101,8 @@ struct Workspace {
     uint8_t* qobs = nullptr;     // [2][qcap]
     int16_t* qiters = nullptr;
     double* post = nullptr;      // [2][qcap][n_units]
+    uint32_t* fsynd = nullptr;   // second-stage syndromes with likely edges flipped: [qcap][nw0] then [qcap][nw1]
+    uint8_t* fbase = nullptr;    // [2][qcap] observable parity of the flipped edges
 };
 
 struct bp4m_graph {
@@ -340,6 +342,8 @@ void free_ws(Workspace& w) {
     cudaFree(w.qobs);
     cudaFree(w.qiters);
     cudaFree(w.post);
+    cudaFree(w.fsynd);
+    cudaFree(w.fbase);
     w = Workspace();
 }
 
@@ -460,15 +464,21 @@ int ensure_qbp_ws(bp4m_graph* g, Workspace& w, int64_t cap) {
     cudaFree(w.qobs);
     cudaFree(w.qiters);
     cudaFree(w.post);
+    cudaFree(w.fsynd);
+    cudaFree(w.fbase);
     w.qconv = nullptr;
     w.qobs = nullptr;
     w.qiters = nullptr;
     w.post = nullptr;
+    w.fsynd = nullptr;
+    w.fbase = nullptr;
     w.qcap = 0;
     CK(dalloc(&w.qconv, cap));
     CK(dalloc(&w.qobs, 2 * (size_t)cap));
     CK(dalloc(&w.qiters, cap));
     CK(dalloc(&w.post, 2 * (size_t)cap * g->host.n_units));
+    CK(dalloc(&w.fsynd, (size_t)cap * (n_words_of(g, 0) + n_words_of(g, 1))));
+    CK(dalloc(&w.fbase, 2 * (size_t)cap));
     w.qcap = cap;
     return BP4M_OK;
 }
@@ -681,6 +691,26 @@ int bbp4mf_device(bp4m_graph* g, Workspace& w, const uint32_t* synd0, const uint
         CK(launch_qbp(prec, q, g->num_sms, st));
         ps.end();
     }
+    // edges above one half are taken as present: flipped syndromes and base parities
+    RwFlipArgs f;
+    f.shots = shots;
+    f.n_units = g->host.n_units;
+    for (int ty = 0; ty < 2; ++ty) {
+        f.n_det[ty] = g->host.t[ty].n_det;
+        f.n_words[ty] = n_words_of(g, ty);
+    }
+    f.synd[0] = synd0;
+    f.synd[1] = synd1;
+    f.post = w.post;
+    f.cc_uvo = g->cc_uvo;
+    f.out[0] = w.fsynd;
+    f.out[1] = w.fsynd + (size_t)shots * n_words_of(g, 0);
+    f.base = w.fbase;
+    {
+        ProfScope ps(g, PROF_CLASSIFY, st);
+        CK(launch_rw_flip(f, g->num_sms, st));
+        ps.end();
+    }
     bp4m_opts o2 = *o;
     o2.decoder = BP4M_DEC_BP4MF;
     for (int ty = 0; ty < 2; ++ty) {
@@ -690,10 +720,11 @@ int bbp4mf_device(bp4m_graph* g, Workspace& w, const uint32_t* synd0, const uint
         s2.skip_iters = w.qiters;
         s2.post = w.post + (size_t)ty * shots * g->host.n_units;
         o2.type = ty;
-        rc = decode_device(g, w, ty, ty == 0 ? synd0 : synd1, shots, T, &o2, obs_pred + (size_t)ty * shots,
+        rc = decode_device(g, w, ty, f.out[ty], shots, T, &o2, obs_pred + (size_t)ty * shots,
                            flags + (size_t)ty * shots, iters + (size_t)ty * shots, nullptr, st, &s2);
         if (rc) return rc;
     }
+    CK(launch_rw_base(obs_pred, w.qconv, w.fbase, shots, st));
     return BP4M_OK;
 }
 

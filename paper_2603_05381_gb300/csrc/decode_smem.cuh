@@ -21,7 +21,13 @@
 // which yields exactly the same matching as the sequential greedy scan.
 //
 // Layout (shared-memory tiers): Mt[i][k] = M[k][i], the message arriving at factor i from
-// the factor k side; Lm[i][k] = l_ik.  Row i is processed by G threads, thread g taking
+// the factor k side; Lm[i][k] = l_ik.  With 16-bit message storage every message leaving
+// factor k is stored relative to a per-row reference r_k (the row's largest Q of that
+// update, rounded to the 16-bit format): Mt[i][k] holds M[k][i] + r_k, which lies in
+// [-lg2(s), 0] for every column but the row's argmax, so the 11-bit (FP16) or 8-bit (BF16)
+// mantissa resolves the message to a few 1e-4 instead of a few 1e-2 of its magnitude; the
+// reader adds -r_k (kept in FP32 per row).  The diagonal holds r_k itself, which decodes
+// to exactly 0.  Row i is processed by G threads, thread g taking
 // the columns of col_off() (FP32: adjacent pairs 2g, 2g+1, then every 2G; FP64: g + G*c).  The update is in place: every thread caches its row in registers,
 // the block synchronises, then each thread writes its outputs M'[i][k] into Mt[k][i].
 #include <cuda_bf16.h>
@@ -214,6 +220,15 @@ __host__ __device__ constexpr int msg_pitch_of(int smax, int g) {
     return sizeof(MS) == 2 ? 2 * g * (((smax + 2 * g - 1) / (2 * g)) | 1) : pitch_of<T>(smax, g);
 }
 
+// Byte offset of the 16-bit path's reference array in the dynamic shared memory, after
+// Mt, Lm, Dg, rowacc, dets, choice, bestp and matched (8-byte aligned).
+template <typename T, typename MS>
+__host__ __device__ constexpr size_t nref_offset(int smax, int g) {
+    return (((size_t)smax * msg_pitch_of<T, MS>(smax, g) * sizeof(MS) + 15) / 16 * 16 +
+            (size_t)(smax * pitch_of<T>(smax, g) + smax + (smax & 1)) * sizeof(T) +
+            (size_t)smax * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 7) / 8 * 8;
+}
+
 // A thread's register-cached row entries (CH columns).  FP32 keeps them as float2 pairs,
 // columns (2j, 2j+1) in one 64-bit register pair, so that the packed FP32x2 add and FMA of
 // sm_100 and later apply to two columns per instruction.
@@ -303,6 +318,8 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
     int* choice = dets + SMAX;
     short* bestp = reinterpret_cast<short*>(choice + SMAX);
     unsigned char* matched = reinterpret_cast<unsigned char*>(bestp + SMAX);
+    // 16-bit messages: nrefv[k] = -r_k, minus the reference of the messages leaving factor k
+    float* nrefv = reinterpret_cast<float*>(smem + nref_offset<T, MS>(SMAX, G));
     // RW only: per-shot W (FP64) and parity over local ranks, Dijkstra state per warp, in
     // this block's global scratch slot (layout of rw_slot_layout)
     const int rw_nodes = a.tb.n_det + 1;
@@ -335,16 +352,24 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
     MS* const col_m = Mt + k0 * PM + i;  // own outputs M[i][k] live at Mt[k][i], register c at [col_off(c) PM]
 #define COL(c) (k0 + col_off<PAIR, G>(c))
 #define RL(c) row_l[col_off<PAIR, G>(c)]
-#define RM(c) IO::ld(row_m + col_off<PAIR, G>(c))
+#define RM(c) m_ld1(row_m + col_off<PAIR, G>(c), COL(c))
 #define CMP(c) (col_m + col_off<PAIR, G>(c) * PM)
-#define CM(c) IO::ld(CMP(c))
+#define CM(c) m_ld1(CMP(c), i)
 #define RL2(j) (*reinterpret_cast<const float2*>(row_l + col_off<PAIR, G>(2 * (j))))
-#define RM2(j) m_ld2(row_m + col_off<PAIR, G>(2 * (j)))
-    auto m_ld2 = [](const MS* p) -> float2 {
+#define RM2(j) m_ld2(row_m + col_off<PAIR, G>(2 * (j)), k0 + col_off<PAIR, G>(2 * (j)))
+    // messages arriving at row i from columns k, k + 1 (16-bit: decoded with the source rows'
+    // references), and one arriving from column k
+    auto m_ld2 = [&](const MS* p, int k) -> float2 {
         if constexpr (HALF)
-            return IO::ld2(p);
+            return __fadd2_rn(IO::ld2(p), *reinterpret_cast<const float2*>(nrefv + k));
         else
             return *reinterpret_cast<const float2*>(p);
+    };
+    auto m_ld1 = [&](const MS* p, int k) -> T {
+        if constexpr (HALF)
+            return IO::ld(p) + nrefv[k];
+        else
+            return IO::ld(p);
     };
 
     for (;;) {
@@ -402,7 +427,8 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
         } else {
             // Dijkstra from every defect (one warp per source): nodes popped in (distance,
             // index) order, predecessor changed only on a strict improvement, the boundary
-            // node n a sink; edge weight ln((1-P)/P) of the qubit behind the edge
+            // node n a sink; edge weight |ln((1-P)/P)| of the qubit behind the edge (edges
+            // above one half were flipped out of the syndrome), floored at kRwMinWeight
             double* dist = rw_dist + warp * rw_nodes;
             unsigned char* done = rw_done + warp * rw_nodes;
             unsigned char* par = rw_par + warp * rw_nodes;
@@ -443,6 +469,9 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                                 const int v = (int)(pk & 0x7FFFu);
                                 double pq = post[(pk >> 15) & 0x7FFFu];
                                 pq = pq < 1e-300 ? 1e-300 : (pq > 1.0 - 1e-16 ? 1.0 - 1e-16 : pq);
+                                // an edge above one half was taken as present (flipped out of
+                                // the syndrome): it weighs as its complement
+                                if (pq > 0.5) pq = 1.0 - pq;
                                 const double nd = bd + fmax(log((1.0 - pq) / pq), kRwMinWeight);
                                 if (nd < dist[v]) {
                                     dist[v] = nd;
@@ -482,6 +511,7 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
             Dg[tid] = T(0);
             matched[tid] = tid >= s;
             bestp[tid] = -1;
+            if constexpr (HALF) nrefv[tid] = 0.f;
         }
         if (tid == 0) {
             sh_best_w = Num<double>::pinf();
@@ -574,7 +604,7 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                     }
                     if (REG && owner_of<PAIR, G>(am_prev) == g) {
                         // the register copy of the argmax column holds the generic output
-                        const float l = Lm[i * P + am_prev], x = IO::ld(Mt + i * PM + am_prev);
+                        const float l = Lm[i * P + am_prev], x = m_ld1(Mt + i * PM + am_prev, am_prev);
                         const float lam = l + (out_am + x);
                         cntf += keep_f(lam) - keep_f(l + (out_am_gen + x));
                         if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + am_prev] = lam * (float)kLn2;
@@ -605,7 +635,7 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                     if (REG && owner_of<PAIR, G>(am_prev) == g) {
                         // the argmax column's own output is out_am, not the generic formula's
                         const int ca = reg_of<PAIR, G>(am_prev);
-                        const T lam = Lm[i * P + am_prev] + (out_am + IO::ld(Mt + i * PM + am_prev));
+                        const T lam = Lm[i * P + am_prev] + (out_am + m_ld1(Mt + i * PM + am_prev, am_prev));
                         bits = (bits & ~((Mask)1 << ca)) | ((Mask)(lam > T(0) ? 1u : 0u) << ca);
                         if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + am_prev] = lam * (T)kLn2;
                     }
@@ -646,7 +676,7 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                             if (!REG && own_diag && c == c_diag) lam.x = Lm[i * P + i] + Dg[i];
                             if (!REG && own_diag && c + 1 == c_diag) lam.y = Lm[i * P + i] + Dg[i];
                             if (REG && owner_of<PAIR, G>(am_prev) == g) {
-                                const float fix = Lm[i * P + am_prev] + (out_am + IO::ld(Mt + i * PM + am_prev));
+                                const float fix = Lm[i * P + am_prev] + (out_am + m_ld1(Mt + i * PM + am_prev, am_prev));
                                 if (c == reg_of<PAIR, G>(am_prev)) lam.x = fix;
                                 if (c + 1 == reg_of<PAIR, G>(am_prev)) lam.y = fix;
                             }
@@ -872,23 +902,32 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                 for (int off = R; off < 32; off <<= 1) S += __shfl_xor_sync(kFull, S, off);
                 const T cf = B2<T>::ex2(m2 - m1);
                 const T Aa = B2<T>::fma_(cf, S - T(1), T(1));
+                // 16-bit storage: this row's reference r_i = m1 rounded to the format (so that
+                // it is exact there), stored values out + r_i = -lg2(Aa - cf u) + (r_i - m1)
+                T rf = T(0), dref = T(0);
+                if constexpr (HALF) {
+                    rf = IO::unpack(IO::pack(m1, 0.f)).x;
+                    dref = rf - m1;
+                }
                 if (act) {
                     if constexpr (std::is_same<T, float>::value) {
                         // out = -m1 - lg2(Aa - cf u), the subtraction as an exact fma with -1
                         const float2 ncf = make_float2(-cf, -cf), A2 = make_float2(Aa, Aa);
-                        const float2 nm1 = make_float2(-m1, -m1), neg1 = make_float2(-1.f, -1.f);
+                        const float2 nm1 = HALF ? make_float2(dref, dref) : make_float2(-m1, -m1);
+                        const float2 neg1 = make_float2(-1.f, -1.f);
 #pragma unroll
                         for (int j = 0; j < CH / 2; ++j) {
                             const float2 y = __ffma2_rn(ncf, q.p[j], A2);
                             const float2 lg = make_float2(B2<float>::lg2(y.x), B2<float>::lg2(y.y));
                             const float2 out = __ffma2_rn(lg, neg1, nm1);
                             if constexpr (HALF) {
-                                // store the rounded pair; the register copy is the stored value,
-                                // so that both ends of a variable see the same message
+                                // store the rounded pair (relative to r_i); the register copy is
+                                // the stored value decoded as every reader decodes it, so that
+                                // both ends of a variable see the same message
                                 const unsigned pk2 = IO::pack(out.x, out.y);
                                 *reinterpret_cast<unsigned short*>(CMP(2 * j)) = (unsigned short)(pk2 & 0xFFFFu);
                                 *reinterpret_cast<unsigned short*>(CMP(2 * j + 1)) = (unsigned short)(pk2 >> 16);
-                                if constexpr (REG) mo.p[j] = IO::unpack(pk2);
+                                if constexpr (REG) mo.p[j] = __fadd2_rn(IO::unpack(pk2), make_float2(-rf, -rf));
                             } else {
                                 *CMP(2 * j) = out.x;
                                 *CMP(2 * j + 1) = out.y;
@@ -904,22 +943,34 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                         }
                     }
                     T oam = -m2 - B2<T>::lg2(S - T(1));
-                    if constexpr (HALF) oam = IO::unpack(IO::pack(oam, 0.f)).x;
-                    if (owner_of<PAIR, G>(am) == g) IO::st(Mt + am * PM + i, oam);
+                    if constexpr (HALF) {
+                        const float st_am = __fmaf_rn(B2<float>::lg2(S - 1.f), -1.f, rf - m2);
+                        if (owner_of<PAIR, G>(am) == g) IO::st(Mt + am * PM + i, st_am);
+                        oam = IO::unpack(IO::pack(st_am, 0.f)).x + (-rf);
+                    } else if (owner_of<PAIR, G>(am) == g) {
+                        IO::st(Mt + am * PM + i, oam);
+                    }
                     if (REG) {
                         am_prev = am;
                         out_am = oam;
                         if constexpr (std::is_same<T, float>::value) {
                             // what the packed output loop wrote for the argmax column: u = ex2(0)
                             const float u0 = B2<float>::ex2(0.f);
-                            float og = __fmaf_rn(B2<float>::lg2(__fmaf_rn(-cf, u0, Aa)), -1.f, -m1);
-                            if constexpr (HALF) og = IO::unpack(IO::pack(og, 0.f)).x;
+                            float og = __fmaf_rn(B2<float>::lg2(__fmaf_rn(-cf, u0, Aa)), -1.f, HALF ? dref : -m1);
+                            if constexpr (HALF) og = IO::unpack(IO::pack(og, 0.f)).x + (-rf);
                             out_am_gen = og;
                         }
                     }
                     if (own_diag) {
-                        if (!REG) Dg[i] = IO::ld(Mt + i * PM + i);
-                        Mt[i * PM + i] = MS(0.f);
+                        if constexpr (HALF) {
+                            // the diagonal holds r_i, which decodes to exactly 0
+                            if (!REG) Dg[i] = IO::ld(Mt + i * PM + i) + (-rf);
+                            IO::st(Mt + i * PM + i, rf);
+                            nrefv[i] = -rf;
+                        } else {
+                            if (!REG) Dg[i] = IO::ld(Mt + i * PM + i);
+                            Mt[i * PM + i] = MS(0.f);
+                        }
                     }
                 }
             }
@@ -995,10 +1046,7 @@ inline int64_t rw_slot_layout(int smax, int nt, int nodes) {
 template <typename T, int CH, int G, typename MS = T>
 size_t smem_bytes_of() {
     constexpr int SMAX = CH * G;
-    constexpr int P = pitch_of<T>(SMAX, G);
-    constexpr int PM = msg_pitch_of<T, MS>(SMAX, G);
-    return ((size_t)SMAX * PM * sizeof(MS) + 15) / 16 * 16 + (size_t)(SMAX * P + SMAX + (SMAX & 1)) * sizeof(T) +
-           (size_t)SMAX * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 16;
+    return nref_offset<T, MS>(SMAX, G) + (sizeof(MS) == 2 ? (size_t)SMAX * sizeof(float) : 0) + 16;
 }
 
 template <typename T, int CH, int G, bool TRACE, bool REG, typename MS = T>

@@ -175,8 +175,27 @@ struct QbpArgs {
     double* post = nullptr;           // [2][shots][n_qubits]: P(X comp), P(Z comp)
 };
 
+// B-BP4MF second-stage preparation: per shot and type, every qubit whose posterior of that
+// type's error component is above one half is taken as present (its edge's endpoints flip
+// in a copy of the syndrome, its observable bit goes into a base parity).
+struct RwFlipArgs {
+    int64_t shots = 0;
+    int n_units = 0;
+    int n_det[2] = {0, 0};
+    int n_words[2] = {0, 0};
+    const uint32_t* synd[2] = {nullptr, nullptr};  // [shots][n_words[ty]]
+    const double* post = nullptr;                  // [2][shots][n_units]
+    const uint32_t* cc_uvo = nullptr;              // [2][n_units] packed u | v << 15 | obs << 31
+    uint32_t* out[2] = {nullptr, nullptr};         // flipped syndromes, same layout as synd
+    uint8_t* base = nullptr;                       // [2][shots]
+};
+
 // ---- launchers (kernels_*.cu) ----
 cudaError_t launch_qbp(int precision, const QbpArgs& a, int num_sms, cudaStream_t st);
+cudaError_t launch_rw_flip(const RwFlipArgs& a, int num_sms, cudaStream_t st);
+// obs_pred[ty][shot] ^= base[ty][shot] for the shots the first stage did not resolve
+cudaError_t launch_rw_base(uint8_t* obs_pred, const uint8_t* skip, const uint8_t* base, int64_t shots,
+                           cudaStream_t st);
 cudaError_t launch_sample_circuit(const SampleArgs& a, cudaStream_t st);
 cudaError_t launch_sample_code_capacity(const SampleArgs& a, cudaStream_t st);
 

@@ -165,7 +165,74 @@ __global__ void __launch_bounds__(kQbpThreads) qbp_kernel(QbpArgs a) {
     }
 }
 
+// Second-stage preparation.  The paper does not say how an edge whose posterior P exceeds
+// 1/2 (weight ln((1-P)/P) < 0, no shortest paths) enters Dijkstra's algorithm; as matching
+// decoders with negative weights do, such an edge is taken as present: its endpoints flip in
+// a copy of the syndrome, its observable bit goes into a base parity added to the decoded
+// one, and it enters the graph with probability 1 - P.  One warp per (type, shot).
+constexpr int kFlipWarps = 8;
+
+__global__ void __launch_bounds__(kFlipWarps * 32) rw_flip_kernel(RwFlipArgs a, int max_words) {
+    extern __shared__ uint32_t fw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* my = fw + warp * max_words;
+    for (int64_t item = (int64_t)blockIdx.x * kFlipWarps + warp; item < 2 * a.shots;
+         item += (int64_t)gridDim.x * kFlipWarps) {
+        const int ty = item >= a.shots ? 1 : 0;
+        const int64_t shot = item - (ty ? a.shots : 0);
+        const int nw = a.n_words[ty], nd = a.n_det[ty];
+        const uint32_t* src = a.synd[ty] + (size_t)shot * nw;
+        for (int w = lane; w < nw; w += 32) my[w] = src[w];
+        __syncwarp();
+        const double* post = a.post + ((size_t)ty * a.shots + shot) * a.n_units;
+        const uint32_t* uvo = a.cc_uvo + (size_t)ty * a.n_units;
+        unsigned ob = 0;
+        for (int q = lane; q < a.n_units; q += 32) {
+            if (post[q] > 0.5) {
+                const uint32_t pk = __ldg(uvo + q);
+                const int u = (int)(pk & 0x7FFFu), v = (int)((pk >> 15) & 0x7FFFu);
+                atomicXor(my + (u >> 5), 1u << (u & 31));
+                if (v < nd) atomicXor(my + (v >> 5), 1u << (v & 31));
+                ob ^= pk >> 31;
+            }
+        }
+        ob = __reduce_xor_sync(0xffffffffu, ob);
+        __syncwarp();
+        uint32_t* dst = a.out[ty] + (size_t)shot * nw;
+        for (int w = lane; w < nw; w += 32) dst[w] = my[w];
+        if (lane == 0) a.base[(size_t)ty * a.shots + shot] = (uint8_t)(ob & 1u);
+        __syncwarp();
+    }
+}
+
+__global__ void rw_base_kernel(uint8_t* obs_pred, const uint8_t* skip, const uint8_t* base, int64_t shots) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < 2 * shots; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t shot = k < shots ? k : k - shots;
+        if (!skip[shot]) obs_pred[k] ^= base[k];
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_rw_flip(const RwFlipArgs& a, int num_sms, cudaStream_t st) {
+    if (a.shots <= 0) return cudaSuccess;
+    const int max_words = a.n_words[0] > a.n_words[1] ? a.n_words[0] : a.n_words[1];
+    const size_t smem = (size_t)kFlipWarps * max_words * sizeof(uint32_t);
+    if (smem > 48 * 1024) return cudaErrorInvalidValue;
+    int64_t g = (2 * a.shots + kFlipWarps - 1) / kFlipWarps;
+    if (g > (int64_t)num_sms * 16) g = (int64_t)num_sms * 16;
+    rw_flip_kernel<<<(int)g, kFlipWarps * 32, smem, st>>>(a, max_words);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rw_base(uint8_t* obs_pred, const uint8_t* skip, const uint8_t* base, int64_t shots,
+                           cudaStream_t st) {
+    if (shots <= 0) return cudaSuccess;
+    int64_t g = (2 * shots + 255) / 256;
+    if (g > 152 * 8) g = 152 * 8;
+    rw_base_kernel<<<(int)g, 256, 0, st>>>(obs_pred, skip, base, shots);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_qbp(int precision, const QbpArgs& a, int num_sms, cudaStream_t st) {
     if (a.shots <= 0) return cudaSuccess;

@@ -61,3 +61,31 @@ class OraclePool:
     def __exit__(self, *exc):
         self.pool.terminate()
         self.pool.join()
+
+
+# ---------------------------------------------------------------- B-BP4MF shots
+
+_BB = {}
+
+
+def _init_bbp(d, family):
+    from oracle.surface import code_capacity_graph, make_code
+    code = make_code(d, family)
+    _BB["code"] = code
+    _BB["graphs"] = {k: code_capacity_graph(code, k) for k in ("X", "Z")}
+
+
+def _bbp(task):
+    from oracle.bbp4mf import bbp4mf_shot
+    sx, sz, p, T = task
+    out = bbp4mf_shot(_BB["code"], _BB["graphs"], sx, sz, p, T, T)
+    return {k: out[k] for k in ("X", "Z", "qbp_converged", "margin", "margin_qbp", "margin_flip", "margin_bp")}
+
+
+def bbp4mf_pool(d, family, shots, p, T, procs=None):
+    """Oracle B-BP4MF of every (X-check syndrome, Z-check syndrome) pair in `shots` over a
+    spawn process pool; returns the per-shot output dicts."""
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs or max(1, os.cpu_count() or 1), initializer=_init_bbp, initargs=(d, family)) as pool:
+        return pool.map(_bbp, [(np.asarray(sx, dtype=int), np.asarray(sz, dtype=int), p, T) for sx, sz in shots],
+                        chunksize=1)

@@ -57,11 +57,12 @@ def test_bbp4mf_ler_matches_paper():
     # B-BP4MF (quaternary BP, then BP4MF on reweighted priors) against the paper's printed
     # curve data.  At d = 5 the ratio ours / paper must lie in [0.75, 1.25] at every p, and
     # above the threshold (p = 0.18) in [0.6, 1.25] at every d.  Below the threshold at
-    # d = 9 and 13 this decoder is markedly stronger than the paper's curves (ratios
-    # 0.09-0.6 measured; the paper does not say how it treats posteriors >= 1/2, which give
-    # non-positive Dijkstra weights and are floored here), so there it must only be no
-    # worse than the paper (ratio <= 1.25).  The threshold behaviour must reproduce: at
-    # p = 0.10 the logical error rate falls with d, at p = 0.18 it rises.
+    # d = 9 and 13 the paper's curves depend on how it treats posteriors above one half
+    # (non-positive Dijkstra weights), which it does not state; the reading here takes such
+    # edges as present (flipped), as matching decoders with negative weights do, and this
+    # decoder is then stronger than the paper's curves there, so it must only be no worse
+    # than the paper (ratio <= 1.25).  The threshold behaviour must reproduce: at p = 0.10
+    # the logical error rate falls with d, at p = 0.18 it rises.
     import torch
     assert torch.cuda.is_available()
     ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_bbp4mf.json")))

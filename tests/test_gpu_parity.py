@@ -395,17 +395,19 @@ def test_unrotated_sampler_and_decoding(torch):
 # ------------------------------------------------------------------ B-BP4MF
 
 
-# (precision, d, p, shots, minimum agreement): d = 5 covers the smallest tiers; d = 17 at
-# p = 0.15 gives 60-100 unsatisfied checks per type (FP64 tiers 2-3), d = 21 at p = 0.155
-# about 130 (FP32 tiers 5-7)
-BBP_CASES = [("fp64", 5, 0.1, 300, 0.99), ("fp32", 5, 0.1, 300, 0.97),
-             ("fp64", 17, 0.15, 12, 0.9), ("fp32", 21, 0.155, 8, 0.85)]
+# B-BP4MF against the oracle shot by shot.  A shot may differ only where the oracle's
+# decision margin allows a rounding to change the outcome: the first stage's posterior gap
+# (relative), an edge posterior's distance from the flip threshold 1/2, or the second
+# stage's BP4MF margin (greedy and marginalization gaps), each below the precision's
+# tolerance.  d = 5 covers the smallest tiers; d = 17 at p = 0.15 gives 60-100 unsatisfied
+# checks per type (FP64 tiers 2-3), d = 21 at p = 0.155 about 130 (FP32 tiers 5-7).
+BBP_TAU = {"fp64": {"qbp": 1e-9, "flip": 1e-9, "bp": 1e-9}, "fp32": {"qbp": 1e-4, "flip": 1e-4, "bp": 1e-2}}
+BBP_CASES = [("fp64", 5, 0.1, 300), ("fp32", 5, 0.1, 300), ("fp64", 17, 0.15, 200), ("fp32", 21, 0.155, 100)]
 
 
-@pytest.mark.parametrize("prec,d,p,n,min_agree", BBP_CASES)
-def test_bbp4mf_matches_oracle(torch, prec, d, p, n, min_agree):
-    from oracle.bbp4mf import bbp4mf_shot
-    from oracle.surface import unrotated_code
+@pytest.mark.parametrize("prec,d,p,n", BBP_CASES)
+def test_bbp4mf_matches_oracle(torch, prec, d, p, n):
+    from oracle_pool import bbp4mf_pool
     T = 25
     g = pkg.Graph(d, "code_capacity", p, family="unrotated")
     info = g.info()
@@ -416,14 +418,20 @@ def test_bbp4mf_matches_oracle(torch, prec, d, p, n, min_agree):
     g.decode_bbp4mf(flat, T, pkg.make_opts(precision=prec), pred, flags)
     torch.cuda.synchronize()
     pred, flags = pred.cpu().numpy(), flags.cpu().numpy()
-    code = unrotated_code(d)
-    graphs = {k: code_capacity_graph(code, k) for k in ("X", "Z")}
     sz = as_bool(synds[0], info["n_det"][0])   # Z-checks
     sx = as_bool(synds[1], info["n_det"][1])   # X-checks
-    agree = stage = 0
-    for k in range(n):
-        out = bbp4mf_shot(code, graphs, sx[k].astype(int), sz[k].astype(int), p, T, T)
-        agree += int(out["X"] == pred[0, k] and out["Z"] == pred[1, k])
-        stage += int(bool(out["qbp_converged"]) == bool(flags[0, k] & 8))
-    print("B-BP4MF %s d=%d p=%.3f: %d/%d shots agree, first stage agrees on %d" % (prec, d, p, agree, n, stage))
-    assert agree >= min_agree * n and stage >= min_agree * n
+    ref = bbp4mf_pool(d, "unrotated", list(zip(sx, sz)), p, T)
+    tau = BBP_TAU[prec]
+    bad, exempt = [], 0
+    for k, out in enumerate(ref):
+        same = (out["X"] == pred[0, k] and out["Z"] == pred[1, k]
+                and bool(out["qbp_converged"]) == bool(flags[0, k] & 8))
+        tight = out["margin_qbp"] < tau["qbp"] or out["margin_flip"] < tau["flip"] or out["margin_bp"] < tau["bp"]
+        exempt += tight
+        if not same and not tight:
+            bad.append((k, out["margin_qbp"], out["margin_flip"], out["margin_bp"]))
+    print("B-BP4MF %s d=%d p=%.3f: %d/%d shots outside the margin rule, %d shots within it"
+          % (prec, d, p, len(bad), n, exempt))
+    assert not bad, bad[:5]
+    # the rule has teeth: most shots are not exempt
+    assert exempt <= n // 4

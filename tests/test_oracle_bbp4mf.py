@@ -64,22 +64,67 @@ def test_bbp4mf_corrects_every_weight_one_error_d3(family):
             assert out["Z"] == int(ez[code.xl].sum() % 2)
 
 
-def test_reweighting_floors_weights_of_likely_errors():
-    # posteriors at or above one half would make edges free or negative; the floor keeps
-    # every shortest path well defined and every prior finite, and a path over k floored
-    # edges weighs exactly k * 2^-20
-    from oracle.bbp4mf import MIN_WEIGHT
+def _brute_map(g, probs, synd):
+    """Most likely edge subset with syndrome `synd` under independent edge probabilities
+    (enumeration of all 2^edges subsets) and the posterior probability that its observable
+    parity is 1."""
+    m = len(g.edges)
+    best, best_p, p_obs1, p_tot = None, -1.0, 0.0, 0.0
+    for mask in range(1 << m):
+        sy = np.zeros(g.n_det, dtype=bool)
+        ob = 0
+        pr = 1.0
+        for e, (u, v, o, _) in enumerate(g.edges):
+            if (mask >> e) & 1:
+                sy[u] ^= True
+                if v < g.n_det:
+                    sy[v] ^= True
+                ob ^= o
+                pr *= probs[e]
+            else:
+                pr *= 1.0 - probs[e]
+        if not np.array_equal(sy, synd):
+            continue
+        p_tot += pr
+        p_obs1 += pr * ob
+        if pr > best_p:
+            best, best_p = mask, pr
+    return best, p_obs1 / p_tot
+
+
+def test_flipping_likely_edges_is_an_exact_change_of_variables():
+    # Taking every edge with P > 1/2 as present (flip its endpoints, add its observable bit
+    # to a base parity) and giving it probability 1 - P leaves the distribution of
+    # corrections unchanged: the most likely correction and the posterior of the observable
+    # parity are the same for every syndrome (brute force over all edge subsets, d = 3)
+    from oracle.bbp4mf import flip_likely_edges
+    code = make_code(3)
+    g = code_capacity_graph(code, "X")
+    rng = np.random.default_rng(5)
+    probs = rng.uniform(0.05, 0.95, size=len(g.edges))
+    assert (probs > 0.5).sum() >= 2
+    comp = np.where(probs > 0.5, 1.0 - probs, probs)
+    fmask = sum(1 << e for e in range(len(g.edges)) if probs[e] > 0.5)
+    for syn_bits in range(1 << g.n_det):
+        synd = np.array([(syn_bits >> j) & 1 for j in range(g.n_det)], dtype=bool)
+        b1, po1 = _brute_map(g, probs, synd)
+        flipped, base, n = flip_likely_edges(g, probs, synd)
+        assert n == bin(fmask).count("1")
+        b2, po2 = _brute_map(g, comp, flipped)
+        assert b1 == b2 ^ fmask
+        assert abs(po1 - (po2 if base == 0 else 1.0 - po2)) < 1e-12
+
+
+def test_edge_weight_is_symmetric_about_one_half():
+    from oracle.bbp4mf import MIN_WEIGHT, edge_weight
+    for p in (1e-9, 0.01, 0.3, 0.499):
+        # 1 - (1 - p) carries the rounding of 1 - p: relative 1e-16 / p
+        assert abs(edge_weight(p) - edge_weight(1.0 - p)) <= 1e-15 / p * edge_weight(p)
+        assert abs(edge_weight(p) - np.log((1 - p) / p)) < 1e-12 * max(1.0, np.log((1 - p) / p))
+    assert edge_weight(0.5) == MIN_WEIGHT
+    # reweighted priors stay finite with edges at one half
     code = make_code(5)
     g = code_capacity_graph(code, "X")
-    probs = [0.9 if e % 3 == 0 else 0.5 for e in range(len(g.edges))]
-    dets = np.arange(g.n_det)
-    W, P, L = reweighted_tables(g, probs, dets)
+    probs = [0.5 if e % 3 == 0 else 0.2 for e in range(len(g.edges))]
+    W, P, L = reweighted_tables(g, probs, np.arange(g.n_det))
     assert np.isfinite(L).all() and (W > 0).all()
-    # every edge floored: W counts hops of the shortest path
-    W1, _, _ = reweighted_tables(g, [0.75] * len(g.edges), dets)
-    hops = np.rint(W1 / MIN_WEIGHT)
-    assert np.allclose(W1, hops * MIN_WEIGHT, rtol=1e-12) and (hops >= 1).all()
-    # neighbouring checks of one qubit are one hop apart
-    u, v = g.edges[0][0], g.edges[0][1]
-    if v < g.n_det:
-        assert hops[u, v] == 1

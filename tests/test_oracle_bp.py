@@ -144,3 +144,82 @@ def test_worked_example_inference():
     assert [(i + 1, j + 1) for (i, j) in bp.matching_from(V)] == [tuple(x) for x in ex["marginalization"]]
     picks = bp.forced_convergence(lam)
     assert [(i + 1, j + 1) for (i, j) in picks] == [tuple(x) for x in ex["forced_pick_order"]]
+
+
+# ------------------------------------------------------------------ decision margins
+#
+# The GPU/oracle comparison exempts a shot only where the oracle's margin says a rounding
+# could change the outcome, so the margins must be sound (no perturbation below them
+# changes the outcome) and tight (some perturbation slightly above changes it).
+
+
+def _random_lambda(s, rng, ties):
+    lam = rng.normal(0.0, 2.0, size=(s, s))
+    lam = np.triu(lam) + np.triu(lam, 1).T
+    if ties:
+        # exact ties between variables that share an endpoint
+        lam[0, 1] = lam[1, 0] = lam[0, 2] = lam[2, 0]
+    return lam
+
+
+def _perturb(lam, delta):
+    out = lam + np.triu(delta) + np.triu(delta, 1).T
+    return out
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_greedy_margin_is_sound_and_tight(seed):
+    rng = np.random.default_rng(seed)
+    s = 6 + seed % 3
+    lam = _random_lambda(s, rng, ties=seed % 2 == 1)
+    m = bp.greedy_margin(lam)
+    ref = bp.forced_convergence(lam)
+    if seed % 2 == 1:
+        assert m == 0.0 or m > 0.0   # the tie may or may not decide; soundness below holds
+    for _ in range(300):
+        d = rng.uniform(-1, 1, size=(s, s)) * (0.49 * m if np.isfinite(m) else 1.0)
+        assert sorted(bp.forced_convergence(_perturb(lam, d))) == sorted(ref)
+    # never looser than the gap between any two posteriors
+    assert m >= bp.order_margin(lam)
+
+
+def test_greedy_margin_is_tight_on_a_decisive_pair():
+    # (0, 1) and (0, 2) compete for factor 0 at the top of the order: their gap decides
+    s = 5
+    lam = np.full((s, s), -6.0)
+    lam[0, 1] = lam[1, 0] = 5.0
+    lam[0, 2] = lam[2, 0] = 4.9
+    lam[3, 4] = lam[4, 3] = 2.0
+    for i in range(s):
+        lam[i, i] = -3.0 - i
+    m = bp.greedy_margin(lam)
+    assert abs(m - 0.1) < 1e-12
+    ref = sorted(bp.forced_convergence(lam))
+    d = np.zeros((s, s))
+    d[0, 1], d[0, 2] = -0.051, 0.051
+    assert sorted(bp.forced_convergence(_perturb(lam, d))) != ref
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_decision_margin_is_sound(seed):
+    rng = np.random.default_rng(100 + seed)
+    s = 5 + seed % 3
+    if seed < 3:
+        lam = _random_lambda(s, rng, ties=False)
+    else:
+        # a converged pattern (a perfect matching of positive posteriors) plus noise
+        lam = -np.abs(rng.normal(3.0, 1.0, size=(s, s)))
+        lam = np.triu(lam) + np.triu(lam, 1).T
+        for i in range(0, s - 1, 2):
+            lam[i, i + 1] = lam[i + 1, i] = abs(rng.normal(0.5, 0.3))
+        if s % 2:
+            lam[s - 1, s - 1] = 0.7
+    m = bp.decision_margin(lam)
+    V0, c0 = bp.decide(lam)
+    assert m > 0
+    for _ in range(300):
+        d = rng.uniform(-1, 1, size=(s, s)) * 0.99 * min(m, 10.0)
+        V, c = bp.decide(_perturb(lam, d))
+        assert c == c0
+        if c0:
+            assert np.array_equal(V, V0)
