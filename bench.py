@@ -68,7 +68,9 @@ def parse():
     # a second mix of small distances only, where every batch fits the shared-memory tiers
     ap.add_argument("--serve-d-low", default="5,9,13")
     ap.add_argument("--serve-requests", type=int, default=200)
-    ap.add_argument("--serve-load", type=float, default=0.5)
+    # offered loads as fractions of the measured capacity (comma-separated), one Poisson
+    # stream of --serve-requests requests each
+    ap.add_argument("--serve-load", default="0.5")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--no-serve", action="store_true")
     # fused multi-graph decode of circuit and code-capacity graphs (d = 5, 9, 13, 17) with
@@ -242,33 +244,41 @@ def run_serving(args, dev, serve_d):
         graphs[k].decode_batch(sy, T, opts32, o)
     plain_shots = sum(o.shape[0] for _, _, o in burst) / (time.perf_counter() - t0)
     mean_req = 2048.5
-    rate = args.serve_load * cap_shots / mean_req
-    reqs = [make_request() for _ in range(args.serve_requests)]
-    gaps = rng.exponential(1.0 / rate, size=len(reqs))
-    st0 = srv.stats()
-    t0 = time.perf_counter()
-    t_next = t0
-    ids = []
-    for (k, s, o), gap in zip(reqs, gaps):
-        t_next += gap
-        while time.perf_counter() < t_next:
-            pass
-        ids.append(srv.submit(gids[k], s, T, opts, o))
-    infos = [srv.wait(r) for r in ids]
-    wall = time.perf_counter() - t0
+    loads = []
+    for load in [float(x) for x in str(args.serve_load).split(",") if x]:
+        rate = load * cap_shots / mean_req
+        reqs = [make_request() for _ in range(args.serve_requests)]
+        gaps = rng.exponential(1.0 / rate, size=len(reqs))
+        st0 = srv.stats()
+        t0 = time.perf_counter()
+        t_next = t0
+        ids = []
+        for (k, s, o), gap in zip(reqs, gaps):
+            t_next += gap
+            while time.perf_counter() < t_next:
+                pass
+            ids.append(srv.submit(gids[k], s, T, opts, o))
+        infos = [srv.wait(r) for r in ids]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        lat = np.array([i["latency_s"] for i in infos]) * 1e3
+        shots = sum(o.shape[0] for _, _, o in reqs)
+        loads.append({"offered_load": load, "requests": len(reqs), "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+                      "sustained_shots_per_s": shots / wall, "batches": st["batches"] - st0["batches"],
+                      "merged_requests": st["merged_requests"] - st0["merged_requests"]})
     st = srv.stats()
     srv.close()
     for g in graphs:
         g.close()
-    lat = np.array([i["latency_s"] for i in infos]) * 1e3
-    shots = sum(o.shape[0] for _, _, o in reqs)
+    first = loads[0]
     return {"graphs": "rotated memory-Z circuit, d in {%s}, p=%g" % (",".join(map(str, ds)), P),
-            "requests": len(reqs), "request_shots": "uniform 1..4096", "iters": T, "slots": args.serve_slots,
+            "requests": first["requests"], "request_shots": "uniform 1..4096", "iters": T, "slots": args.serve_slots,
+            "precision": args.precision, "admission": "free device memory (no caller budget)",
             "capacity_shots_per_s": cap_shots, "plain_fp32_per_request_shots_per_s": plain_shots,
-            "capacity_vs_plain": cap_shots / plain_shots, "offered_load": args.serve_load,
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "sustained_shots_per_s": shots / wall,
-            "batches": st["batches"] - st0["batches"], "merged_requests": st["merged_requests"] - st0["merged_requests"],
+            "capacity_vs_plain": cap_shots / plain_shots, "offered_load": first["offered_load"],
+            "p50_ms": first["p50_ms"], "p99_ms": first["p99_ms"], "mean_ms": first["mean_ms"],
+            "sustained_shots_per_s": first["sustained_shots_per_s"], "loads": loads,
             "max_inflight_batches": st["max_inflight_batches"]}
 
 

@@ -285,13 +285,18 @@ void bp4m_free_graph(bp4m_graph* g);
    run on its stream, so the slots' batches overlap on the GPU, except that a batch of a
    heavy graph (one whose shots average more than 160 unsatisfied detectors, estimated
    from its edge probabilities when it is added) runs alone: it waits for the batches in
-   flight and holds back new ones until it ends.  Message state and tables stay resident:
-   each slot keeps one workspace per graph it has decoded, sized for max_batch_shots.
-   When the device bytes of all workspaces' per-shot buffers would exceed
-   device_budget_bytes (0: no limit), a slot frees its least recently used workspaces
-   before allocating; a batch that still does not fit fails with BP4M_ENOMEM.  (Scratch
-   of the global-memory tier, for shots with more than 160 unsatisfied detectors, grows
-   on demand outside the budget.)  A graph's per-iteration results are
+   flight and holds back new ones until it ends.  A heavy graph's request is decoded in
+   pieces of at most 512 shots; after each piece the rest of the request goes to the back
+   of the queue, so requests that arrived meanwhile are served between its pieces.
+   Message state and tables stay resident: each slot keeps one workspace per graph it has
+   decoded, sized for max_batch_shots.  Admission by device memory: before a workspace
+   grows, its per-shot buffers must fit device_budget_bytes (summed over all workspaces),
+   or, with device_budget_bytes = 0, leave at least max(1 GiB, 1/32 of the device) of the
+   device's memory free (cudaMemGetInfo); otherwise the slot frees its least recently used
+   workspaces, and a batch that still does not fit fails with BP4M_ENOMEM.  (Scratch of
+   the global-memory tier, for shots with more than 160 unsatisfied detectors, grows on
+   demand outside the budget; its allocation failing fails the batch with BP4M_ENOMEM.)
+   A graph's per-iteration results are
    bit-identical to bp4m_decode_batch on the same syndromes, alone or merged with others.
    bp4m_profile_* does not see the service's launches.  Decoders BP4M and BP4MF (any
    precision); B-BP4MF is BP4M_EUNSUPPORTED. */
@@ -315,7 +320,8 @@ typedef struct {
                                       device_budget_bytes limits; streaming-tier scratch excluded) */
 } bp4m_server_stats_t;
 
-/* n_slots in [1, 64]; max_batch_shots in [1, 2^20].  NULL on error (bp4m_last_error). */
+/* n_slots in [1, 64]; max_batch_shots in [1, 2^20]; device_budget_bytes >= 0 (0: admission by
+   free device memory).  NULL on error (bp4m_last_error). */
 bp4m_server* bp4m_server_create(int n_slots, int64_t max_batch_shots, int64_t device_budget_bytes);
 /* Registers a graph (uploading its tables); returns its id >= 0 or a negative error code.
    The graph must outlive the server. */

@@ -819,7 +819,22 @@ struct SrvRequest {
     int rc = 0;
     std::string err;
     bool done = false;
+    // a request of a heavy graph is decoded in pieces of at most kHeavyPiece shots, each
+    // piece queued behind the requests that arrived meanwhile
+    int64_t taken = 0;       // shots handed to workers
+    int64_t finished = 0;    // shots whose piece has completed
 };
+
+// One piece of a batch: shots [off, off + cnt) of a request.
+struct SrvPiece {
+    SrvRequest* r;
+    int64_t off, cnt;
+};
+
+// Largest piece of a heavy graph's request: a 4096-shot request of a d = 25 circuit takes
+// the whole GPU for most of a second, so it is cut into pieces and requests that arrive
+// meanwhile are served between them.
+constexpr int64_t kHeavyPiece = 512;
 
 struct SrvSlot {
     int index = 0;
@@ -943,8 +958,11 @@ struct bp4m_server {
 
 namespace {
 
-int srv_run_batch(bp4m_server* S, SrvSlot& sl, std::vector<SrvRequest*>& batch, int64_t n, int64_t stamp) {
-    SrvRequest& h = *batch[0];
+// Device bytes that admission keeps free when the service has no explicit budget.
+size_t srv_reserve_bytes(size_t total) { return std::max<size_t>((size_t)1 << 30, total / 32); }
+
+int srv_run_batch(bp4m_server* S, SrvSlot& sl, std::vector<SrvPiece>& batch, int64_t n, int64_t stamp) {
+    SrvRequest& h = *batch[0].r;
     bp4m_graph* g = nullptr;
     bool heavy = false;
     {
@@ -965,13 +983,21 @@ int srv_run_batch(bp4m_server* S, SrvSlot& sl, std::vector<SrvRequest*>& batch, 
     // request would free and reallocate device memory (a device-wide synchronisation that
     // stalls every other slot) each time a larger request arrived
     const int64_t cap = std::max<int64_t>(n, S->max_batch);
-    if (w.cap < cap && S->budget > 0) {
-        // bytes of the per-shot buffers at that capacity (ensure_ws) beyond what this
-        // workspace holds
+    if (w.cap < cap) {
+        // admission: bytes of the per-shot buffers at that capacity (ensure_ws) beyond what
+        // this workspace holds must fit the caller's budget, or with no budget leave at
+        // least srv_reserve_bytes() of the device free; least recently used workspaces of
+        // this slot are freed until they do
         size_t words = 0;
         for (int t = 0; t < g->host.n_types; ++t) words += n_words_of(g, t);
         const int64_t need = (int64_t)((size_t)cap * (words * 4 + 5 * g->host.n_types + kTiers * 4)) - (int64_t)before;
-        while (S->used.load() + need > S->budget) {
+        auto fits = [&]() -> bool {
+            if (S->budget > 0) return S->used.load() + need <= S->budget;
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return false;
+            return (int64_t)free_b - need >= (int64_t)srv_reserve_bytes(total_b);
+        };
+        while (!fits()) {
             int victim = -1;
             int64_t oldest = INT64_MAX;
             for (auto& kv : sl.ws)
@@ -979,7 +1005,9 @@ int srv_run_batch(bp4m_server* S, SrvSlot& sl, std::vector<SrvRequest*>& batch, 
                     oldest = sl.last_use[kv.first];
                     victim = kv.first;
                 }
-            if (victim < 0) return fail(BP4M_ENOMEM, "the batch's workspace does not fit the device budget");
+            if (victim < 0)
+                return fail(BP4M_ENOMEM, S->budget > 0 ? "the batch's workspace does not fit the device budget"
+                                                       : "the batch's workspace does not fit the free device memory");
             S->used -= (int64_t)ws_bytes(sl.ws[victim]);
             free_ws(sl.ws[victim]);
             sl.ws.erase(victim);
@@ -1009,9 +1037,9 @@ int srv_run_batch(bp4m_server* S, SrvSlot& sl, std::vector<SrvRequest*>& batch, 
         sl.h_words = words;
     }
     int64_t off = 0;
-    for (SrvRequest* r : batch) {
-        std::memcpy(sl.h_in + (size_t)off * nw, r->synd.data(), (size_t)r->shots * nw * 4);
-        off += r->shots;
+    for (const SrvPiece& pc : batch) {
+        std::memcpy(sl.h_in + (size_t)off * nw, pc.r->synd.data() + (size_t)pc.off * nw, (size_t)pc.cnt * nw * 4);
+        off += pc.cnt;
     }
     CK(cudaMemcpyAsync(w.synd, sl.h_in, (size_t)n * nw * 4, cudaMemcpyHostToDevice, st));
     rc = decode_device(g, w, ty, w.synd, n, h.iters, &h.opts, w.obs_pred, w.flags, w.iters, nullptr, st);
@@ -1021,11 +1049,12 @@ int srv_run_batch(bp4m_server* S, SrvSlot& sl, std::vector<SrvRequest*>& batch, 
     CK(cudaStreamSynchronize(st));
     S->used += (int64_t)ws_bytes(w) - (int64_t)before;
     off = 0;
-    for (SrvRequest* r : batch) {
-        std::memcpy(r->out_obs, sl.h_out + off, (size_t)r->shots);
-        if (r->out_conv)
-            for (int64_t k = 0; k < r->shots; ++k) r->out_conv[k] = (uint8_t)(sl.h_out[n + off + k] & F_CONVERGED);
-        off += r->shots;
+    for (const SrvPiece& pc : batch) {
+        std::memcpy(pc.r->out_obs + pc.off, sl.h_out + off, (size_t)pc.cnt);
+        if (pc.r->out_conv)
+            for (int64_t k = 0; k < pc.cnt; ++k)
+                pc.r->out_conv[pc.off + k] = (uint8_t)(sl.h_out[n + off + k] & F_CONVERGED);
+        off += pc.cnt;
     }
     return BP4M_OK;
 }
@@ -1035,7 +1064,7 @@ void srv_worker(bp4m_server* S, SrvSlot* sl) {
     cudaSetDevice(S->device);
     int64_t stamp = 0;
     for (;;) {
-        std::vector<SrvRequest*> batch;
+        std::vector<SrvPiece> batch;
         int64_t n = 0;
         {
             std::unique_lock<std::mutex> lk(S->mu);
@@ -1043,12 +1072,19 @@ void srv_worker(bp4m_server* S, SrvSlot* sl) {
             if (S->pending.empty()) return;  // stop requested and nothing left
             SrvRequest* h = S->pending.front();
             S->pending.pop_front();
-            batch.push_back(h);
-            n = h->shots;
+            // a heavy graph's batch is at most one piece; the rest of its request goes to the
+            // back of the queue, behind what arrived meanwhile
+            const int64_t limit = S->heavy[h->graph] ? std::min<int64_t>(kHeavyPiece, S->max_batch) : S->max_batch;
+            const int64_t cnt = std::min<int64_t>(limit, h->shots - h->taken);
+            batch.push_back(SrvPiece{h, h->taken, cnt});
+            h->taken += cnt;
+            n = cnt;
+            if (h->taken < h->shots) S->pending.push_back(h);
             for (auto it = S->pending.begin(); it != S->pending.end();) {
                 SrvRequest* r = *it;
-                if (same_batch(*h, *r) && n + r->shots <= S->max_batch) {
-                    batch.push_back(r);
+                if (r != h && r->taken == 0 && same_batch(*h, *r) && n + r->shots <= limit) {
+                    batch.push_back(SrvPiece{r, 0, r->shots});
+                    r->taken = r->shots;
                     n += r->shots;
                     it = S->pending.erase(it);
                 } else {
@@ -1059,7 +1095,8 @@ void srv_worker(bp4m_server* S, SrvSlot* sl) {
             S->max_inflight = std::max<int64_t>(S->max_inflight, S->inflight);
         }
         const double t0 = now_s();
-        for (SrvRequest* r : batch) r->t_start = t0;
+        for (const SrvPiece& pc : batch)
+            if (pc.off == 0) pc.r->t_start = t0;
         const int rc = srv_run_batch(S, *sl, batch, n, ++stamp);
         const double t1 = now_s();
         {
@@ -1068,14 +1105,20 @@ void srv_worker(bp4m_server* S, SrvSlot* sl) {
             ++S->n_batches;
             S->n_merged += (int64_t)batch.size() - 1;
             if (rc == BP4M_OK) S->shots_done += n;
-            for (SrvRequest* r : batch) {
-                r->t_done = t1;
-                r->batch_shots = n;
+            for (const SrvPiece& pc : batch) {
+                SrvRequest* r = pc.r;
+                r->finished += pc.cnt;
+                r->batch_shots = std::max<int64_t>(r->batch_shots, n);
                 r->slot = sl->index;
-                r->rc = rc;
-                if (rc) r->err = g_last_error;
-                r->done = true;
-                std::vector<uint32_t>().swap(r->synd);
+                if (rc && !r->rc) {
+                    r->rc = rc;
+                    r->err = g_last_error;
+                }
+                if (r->finished == r->shots) {
+                    r->t_done = t1;
+                    r->done = true;
+                    std::vector<uint32_t>().swap(r->synd);
+                }
             }
         }
         S->done_cv.notify_all();
@@ -1244,7 +1287,7 @@ bp4m_server* bp4m_server_create(int n_slots, int64_t max_batch_shots, int64_t de
         return nullptr;
     }
     if (device_budget_bytes < 0) {
-        fail(BP4M_EINVAL, "device_budget_bytes must be >= 0 (0: no limit)");
+        fail(BP4M_EINVAL, "device_budget_bytes must be >= 0 (0: admission by free device memory)");
         return nullptr;
     }
     bp4m_server* S = new (std::nothrow) bp4m_server();

@@ -401,7 +401,10 @@ def test_unrotated_sampler_and_decoding(torch):
 # stage's BP4MF margin (greedy and marginalization gaps), each below the precision's
 # tolerance.  d = 5 covers the smallest tiers; d = 17 at p = 0.15 gives 60-100 unsatisfied
 # checks per type (FP64 tiers 2-3), d = 21 at p = 0.155 about 130 (FP32 tiers 5-7).
-BBP_TAU = {"fp64": {"qbp": 1e-9, "flip": 1e-9, "bp": 1e-9}, "fp32": {"qbp": 1e-4, "flip": 1e-4, "bp": 1e-2}}
+# FP32: the first stage's posteriors carry relative errors of order 1e-6 after 25
+# iterations, the second stage's posteriors absolute errors of order 1e-5 (the FP32 lambda
+# test measures < 1e-6 relative to |l| + 1); the tolerances keep a factor 10-100 above that.
+BBP_TAU = {"fp64": {"qbp": 1e-9, "flip": 1e-9, "bp": 1e-9}, "fp32": {"qbp": 1e-5, "flip": 1e-5, "bp": 1e-3}}
 BBP_CASES = [("fp64", 5, 0.1, 300), ("fp32", 5, 0.1, 300), ("fp64", 17, 0.15, 200), ("fp32", 21, 0.155, 100)]
 
 

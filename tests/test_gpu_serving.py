@@ -130,3 +130,36 @@ def test_rejects_device_buffers_and_bbp4mf(graphs):
     with pytest.raises(pkg.Bp4mError):
         srv.submit(gid, host, T, pkg.make_opts(decoder="bbp4mf"), pred)
     srv.close()
+
+
+def test_heavy_request_is_served_in_pieces(graphs):
+    # a 1536-shot request of the d = 25 circuit (a heavy graph, streaming tier) is decoded in
+    # pieces of at most 512 shots; small requests submitted right after it are served
+    # between its pieces, and every result equals decode alone
+    g_heavy, g_light = graphs[3], graphs[0]
+    heavy = _host_syndromes(g_heavy, 1536, seed=41)
+    light = _host_syndromes(g_light, 400, seed=42)
+    opts = pkg.make_opts(precision="fp32", early_exit=True)
+    srv = pkg.Server(slots=2, max_batch_shots=4096)
+    gid_h, gid_l = srv.add_graph(g_heavy), srv.add_graph(g_light)
+    out_h = np.empty(1536, dtype=np.uint8)
+    conv_h = np.empty(1536, dtype=np.uint8)
+    rid_h = srv.submit(gid_h, heavy, T, opts, out_h, conv_h)
+    small = []
+    for k in range(4):
+        o = np.empty(100, dtype=np.uint8)
+        small.append((srv.submit(gid_l, np.ascontiguousarray(light[100 * k:100 * (k + 1)]), T, opts, o), k, o))
+    info_h = srv.wait(rid_h)
+    infos = [(srv.wait(rid), k, o) for rid, k, o in small]
+    st = srv.stats()
+    srv.close()
+    want_h, want_c = _alone(g_heavy, heavy, opts)
+    assert np.array_equal(out_h, want_h) and np.array_equal(conv_h, want_c)
+    want_l, _ = _alone(g_light, light, opts)
+    for info, k, o in infos:
+        assert np.array_equal(o, want_l[100 * k:100 * (k + 1)])
+    # at least three pieces for the heavy request, and the small requests did not wait for
+    # all of it
+    assert st["batches"] >= 3 + 1
+    assert info_h["batch_shots"] <= 512
+    assert min(info["t_done"] for info, _, _ in infos) < info_h["t_done"]
