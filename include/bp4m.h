@@ -286,7 +286,7 @@ void bp4m_free_graph(bp4m_graph* g);
    heavy graph (one whose shots average more than 160 unsatisfied detectors, estimated
    from its edge probabilities when it is added) runs alone: it waits for the batches in
    flight and holds back new ones until it ends.  A heavy graph's request is decoded in
-   pieces of at most 512 shots; after each piece the rest of the request goes to the back
+   pieces of at most 1024 shots; after each piece the rest of the request goes to the back
    of the queue, so requests that arrived meanwhile are served between its pieces.
    Message state and tables stay resident: each slot keeps one workspace per graph it has
    decoded, sized for max_batch_shots.  Admission by device memory: before a workspace

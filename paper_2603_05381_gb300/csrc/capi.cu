@@ -606,7 +606,7 @@ int decode_device(bp4m_graph* g, Workspace& w, int ty, const uint32_t* synd, int
         // width classes up to the batch's largest defect count; the scratch holds a slot for
         // every resident block of the class that needs most, whatever this batch's count, so
         // that it is reallocated (a device-wide synchronisation) only for a wider slot
-        const GlobalPlan p = global_plan(prec, max_s, g->num_sms);
+        const GlobalPlan p = global_plan(pio, max_s, g->num_sms);
         int rc = ensure_gscratch(w, p.need + (p.gc.n > 1 ? p.need_small : 0));
         if (rc) return rc;
         if (p.gc.n > 1) {
@@ -620,7 +620,7 @@ int decode_device(bp4m_graph* g, Workspace& w, int ty, const uint32_t* synd, int
         a.tier = kGlobalTier;
         ProfScope ps(g, PROF_GLOBAL, st);
         if (p.gc.n == 1) {
-            rc = launch_global_classes(a, p, prec, n_glob, w.sub, w.subctr, shots, w.small + kTiers + kGlobalTier,
+            rc = launch_global_classes(a, p, pio, n_glob, w.sub, w.subctr, shots, w.small + kTiers + kGlobalTier,
                                        g->num_sms, st);
             if (rc) return rc;
         } else {
@@ -650,7 +650,7 @@ int decode_device(bp4m_graph* g, Workspace& w, int ty, const uint32_t* synd, int
                     b.gslot_elems = (int64_t)(p.slot_bytes[c] / esz / 3);
                     b.gsmax = p.gsmax[c];
                     if (small) b.gscratch = static_cast<unsigned char*>(w.gscratch) + p.need;
-                    CK(launch_decode_global(prec, b, small ? cnt : std::min(cnt, p.full[c]), small ? w.aux : st));
+                    CK(launch_decode_global(pio, b, small ? cnt : std::min(cnt, p.full[c]), small ? w.aux : st));
                 }
             CK(cudaEventRecord(w.ev_join, w.aux));
             CK(cudaStreamWaitEvent(st, w.ev_join, 0));
@@ -834,7 +834,7 @@ struct SrvPiece {
 // Largest piece of a heavy graph's request: a 4096-shot request of a d = 25 circuit takes
 // the whole GPU for most of a second, so it is cut into pieces and requests that arrive
 // meanwhile are served between them.
-constexpr int64_t kHeavyPiece = 512;
+constexpr int64_t kHeavyPiece = 1024;
 
 struct SrvSlot {
     int index = 0;
@@ -872,37 +872,40 @@ double expected_defects(const bp4m_graph* g, int ty) {
 }
 
 // Admission of batches to the GPU: shared batches run together, an exclusive batch runs
-// alone.  Waiting exclusive batches go first (a stream of shared batches cannot starve
-// them).
+// alone.  Batches are admitted in the order they reach the gate: a waiting batch is
+// admitted once every batch that arrived before it has been, an exclusive one when nothing
+// is running, a shared one when no exclusive batch is running.  So neither kind starves
+// the other, and the pieces of a heavy request interleave with what arrived between them.
 class GpuGate {
 public:
-    void lock_shared() {
-        std::unique_lock<std::mutex> lk(m_);
-        cv_.wait(lk, [&] { return !excl_ && excl_waiting_ == 0; });
-        ++shared_;
-    }
-    void unlock_shared() {
-        std::lock_guard<std::mutex> lk(m_);
-        if (--shared_ == 0) cv_.notify_all();
-    }
-    void lock() {
-        std::unique_lock<std::mutex> lk(m_);
-        ++excl_waiting_;
-        cv_.wait(lk, [&] { return !excl_ && shared_ == 0; });
-        --excl_waiting_;
-        excl_ = true;
-    }
-    void unlock() {
-        std::lock_guard<std::mutex> lk(m_);
-        excl_ = false;
-        cv_.notify_all();
-    }
+    void lock_shared() { enter(false); }
+    void unlock_shared() { leave(false); }
+    void lock() { enter(true); }
+    void unlock() { leave(true); }
 
 private:
+    void enter(bool excl) {
+        std::unique_lock<std::mutex> lk(m_);
+        const uint64_t me = next_++;
+        waiting_.push_back(me);
+        cv_.wait(lk, [&] { return waiting_.front() == me && (excl ? inside_ == 0 : !excl_inside_); });
+        waiting_.pop_front();
+        ++inside_;
+        excl_inside_ = excl;
+        cv_.notify_all();  // the next waiter may be compatible
+    }
+    void leave(bool excl) {
+        std::lock_guard<std::mutex> lk(m_);
+        --inside_;
+        if (excl) excl_inside_ = false;
+        cv_.notify_all();
+    }
     std::mutex m_;
     std::condition_variable cv_;
-    int shared_ = 0, excl_waiting_ = 0;
-    bool excl_ = false;
+    std::deque<uint64_t> waiting_;
+    uint64_t next_ = 0;
+    int inside_ = 0;
+    bool excl_inside_ = false;
 };
 
 // Holds the gate for one batch (exclusive or shared) until it goes out of scope.
@@ -1258,8 +1261,8 @@ int multi_enqueue(bp4m_multi* m, const std::vector<int64_t>& shots, int plan) {
     a.gscratch = m->gscratch;
     {
         // every width class up to max_defects: the counts stay on the device
-        const GlobalPlan p = global_plan(1, m->max_defects, m->num_sms);
-        const int rc = launch_global_classes(a, p, 1, m->total_cap, m->sub, m->subctr, m->total_cap,
+        const GlobalPlan p = global_plan(m->pio, m->max_defects, m->num_sms);
+        const int rc = launch_global_classes(a, p, m->pio, m->total_cap, m->sub, m->subctr, m->total_cap,
                                              m->small + kTiers + kGlobalTier, m->num_sms, st);
         if (rc) return rc;
     }
@@ -1516,7 +1519,7 @@ bp4m_multi* bp4m_multi_create(int n, bp4m_graph* const* graphs, const int* types
         return bad(fail(BP4M_ECUDA, "upload of the entries failed"));
     // streaming tier: per width class up to max_defects one slot per resident block
     {
-        const GlobalPlan p = global_plan(1, max_defects, m->num_sms);
+        const GlobalPlan p = global_plan(m->pio, max_defects, m->num_sms);
         if (cudaMalloc(&m->gscratch, p.need) != cudaSuccess)
             return bad(fail(BP4M_ENOMEM, "out of memory for the streaming tier's scratch"));
         if (dalloc(&m->sub, (size_t)kMaxGlobalClasses * m->total_cap) != cudaSuccess ||

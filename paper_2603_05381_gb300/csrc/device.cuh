@@ -238,6 +238,9 @@ size_t global_slot_bytes(int precision, int max_s, int* gsmax_out);
 int global_blocks_per_sm(int precision, int max_s);
 cudaError_t launch_decode_global(int precision, const DecodeArgs& a, int slots,
                                  cudaStream_t st);
+// Streaming tier with 16-bit message storage (precision 2 = IEEE half, 3 = bfloat16) for
+// ch columns per lane (kernels_half.cu).
+cudaError_t launch_stream_half(int precision, int ch, const DecodeArgs& a, int slots, cudaStream_t st);
 // Width classes of the global tier for a batch whose largest defect count is max_s: class k
 // takes the shots with smax[k-1] < s <= smax[k] (smax ascending; the last class is max_s's
 // own, the general kernel's when max_s is above the widest streaming variant).

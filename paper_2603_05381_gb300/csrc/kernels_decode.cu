@@ -10,6 +10,7 @@
 #include <cmath>
 
 #include "decode_smem.cuh"
+#include "decode_stream.cuh"
 #include "device.cuh"
 
 namespace bp4m {
@@ -304,459 +305,6 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
     }
 }
 
-// ------------------------------------------------------------------ streaming tier
-//
-// Shots with more unsatisfied detectors than the shared-memory tiers hold.  One warp owns
-// one factor row at a time (its CH*32 columns in registers); the shot's matrices live in a
-// per-block scratch slot in global memory (L2-resident for the sizes this tier meets):
-//   Lg[r][k]     prior l_rk in log2 units, -inf for k >= s          (ld = 32*CH columns)
-//   Mt[b][r][k]  incoming message M[k][r], double buffered (b = iteration parity)
-//   Mo[r][k]     the row's own outputs M[r][k], updated in place by the owning warp
-// The diagonal of Mt is kept 0, so Q_rr = l_rr and lambda_rr = l_rr + Mo[r][r].  Outputs go
-// to Mt[next][k][r]; a batch of W consecutive rows (one per warp) stages them in shared
-// memory and writes W consecutive elements per column k.  Iteration = decision pass
-// (lambda of the previous update, convergence vote, candidates / forced convergence), then
-// the update pass.
-constexpr int kStreamWarps = 16;
-// Blocks per SM: the 256-column variant (shots of up to 256 defects) runs two, so that one
-// block's L2 latency overlaps the other's arithmetic.
-template <typename T, int CH>
-constexpr int kStreamBlocks = (sizeof(T) == 4 && CH <= 8) ? 2 : 1;
-// Warps per block (one row in flight per warp, each with a 3-row prefetch buffer in shared
-// memory): FP32 320 and 384 columns run one 32-warp block per SM (twice the rows in flight
-// per batch and half the batch barriers of 16 warps), 896 and 1024 columns one 12-warp block
-// (the largest count whose prefetch buffers and output stage fit in 227 KB), the others 16.
-template <typename T, int CH>
-constexpr int kStreamWarpsOf = sizeof(T) != 4 ? kStreamWarps : (CH >= 10 && CH <= 12) ? 32 : CH >= 28 ? 12 : kStreamWarps;
-// Row prefetch of the update pass: each warp copies its next row of Lg, Mc and Mo into
-// shared memory (asynchronous copies) while it updates the current one.
-//   1: the row is moved into registers and the next copy issued at once (FP32, <= 256 columns)
-//   2: the row is read in place and the next copy issued after its last read (FP32, 320 to
-//      1024 columns, where the register copy would spill)
-//   0: rows are read from global memory (FP64)
-template <typename T, int CH>
-constexpr int kStreamPrefetch = sizeof(T) != 4 ? 0 : CH <= 8 ? 1 : 2;
-
-// 16-byte asynchronous global->shared copies (cp.async, L2 only), used to fetch a warp's next
-// factor row while it works on the current one
-__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
-    const size_t g = __cvta_generic_to_global(gmem_src);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
-template <typename T>
-__device__ __forceinline__ T warp_max(T v) {
-#pragma unroll
-    for (int off = 16; off; off >>= 1) v = B2<T>::mx(v, __shfl_xor_sync(kFull, v, off));
-    return v;
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-    return v;
-}
-
-template <typename T, int CH, bool TRACE, int W>
-__global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, CH> : 1) decode_stream_kernel(const DecodeArgs a) {
-    constexpr int NTH = W * 32;
-    constexpr int LD = 32 * CH;
-    constexpr int SP = LD + 1;  // stage pitch: odd, so the transposed read is conflict-free
-    // FP32 variants of up to 256 columns prefetch each warp's next row of Lg, Mc and Mo into
-    // shared memory (pf[W][3][LD]) during the current row's update
-    constexpr int PFM = kStreamPrefetch<T, CH>;
-    constexpr bool PF = PFM != 0;
-    extern __shared__ __align__(16) unsigned char smem[];
-    T* const pf = reinterpret_cast<T*>(smem);
-    T* stage = pf + (PF ? W * 3 * LD : 0);                          // [W][SP]
-    double* rowacc = reinterpret_cast<double*>(stage + W * SP + ((W * SP) & 1));
-    int* dets = reinterpret_cast<int*>(rowacc + LD);
-    int* choice = dets + LD;
-    short* bestp = reinterpret_cast<short*>(choice + LD);
-    unsigned char* matched = reinterpret_cast<unsigned char*>(bestp + LD);
-    __shared__ int sh_item, sh_s, sh_best_par, sh_best_forced, sh_improve, sh_use_best;
-    __shared__ double sh_best_w;
-
-    const size_t mat = (size_t)LD * LD;
-    T* slot = reinterpret_cast<T*>(a.gscratch) + (size_t)blockIdx.x * 4 * mat;
-    T* Lg = slot;
-    T* Mtb[2] = {slot + mat, slot + 2 * mat};
-    T* Mo = slot + 3 * mat;
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t count = a.count ? (int64_t)*a.count : a.count_val;
-    const T ainv = (T)(1.0 / a.alpha);
-    const bool full = (a.decoder == 1) || !a.early_exit;
-    T* trl = reinterpret_cast<T*>(a.tr_lambda);
-    const T ninf = Num<T>::ninf();
-    unsigned long long acc_it = 0, acc_msg = 0, acc_def = 0, acc_shots = 0, acc_fc = 0, acc_fcr = 0;
-
-    for (;;) {
-        if (tid == 0) sh_item = atomicAdd(a.next, 1);
-        __syncthreads();
-        const int item = sh_item;
-        if (item >= count) break;
-        const ItemCtx ic = resolve_item(a, a.list ? (int64_t)a.list[item] : (int64_t)item);
-        const int64_t shot = ic.shot;
-        const int n = ic.tb.n_det;
-        const T* __restrict__ Ltab = Num<T>::L(ic.tb);
-        if (warp == 0) {
-            const int s0 = compact_defects(ic.synd + (size_t)shot * ic.tb.n_words, ic.tb.n_words, dets, LD, lane);
-            if (lane == 0) sh_s = s0;
-        }
-        __syncthreads();
-        const int s = sh_s;
-        if (s > LD || s < 2) {
-            if (tid == 0 && a.ctr) atomicAdd(a.ctr + C_ERRORS, 1ull);
-            continue;
-        }
-        const bool tr_on = TRACE && s <= a.s_cap;
-        for (int r = warp; r < s; r += W) {
-            const T* trow = Ltab + (size_t)dets[r] * n;
-            for (int k = lane; k < LD; k += 32) {
-                Lg[(size_t)r * LD + k] = k < s ? (T)(__ldg(trow + dets[k]) * (T)kLog2e) : ninf;
-                Mtb[0][(size_t)r * LD + k] = T(0);
-                Mtb[1][(size_t)r * LD + k] = T(0);
-                Mo[(size_t)r * LD + k] = T(0);
-            }
-        }
-        for (int r = tid; r < LD; r += NTH) {
-            matched[r] = r >= s;
-            bestp[r] = -1;
-        }
-        if (tid == 0) {
-            sh_best_w = Num<double>::pinf();
-            sh_best_par = 0;
-            sh_best_forced = 0;
-            sh_use_best = 0;
-        }
-        __syncthreads();
-
-        int cur = 0;
-        int t = 0;
-        bool any_conv = false, forced_ran = false;
-        int out_par = 0, out_forced = 0, out_from_best = 0;
-
-        // BP4M with early exit: the decisions of lambda^t are taken inside the update pass that
-        // reads the same rows (Lg, Mc, Mo once per iteration instead of twice); only the last
-        // iteration, which may need forced convergence, keeps the separate decision pass
-        const bool merged = !TRACE && a.decoder == 0 && a.early_exit;
-        for (;;) {
-            const T* Mc = Mtb[cur];
-            const bool fuse = merged && t > 0 && t < a.T;
-            if (t > 0 && !fuse) {
-                // ---- decisions of lambda^t = l + (M[r][k] + M[k][r])
-                int ok_all = 1;
-                for (int r = warp; r < s; r += W) {
-                    const T* lrow = Lg + (size_t)r * LD;
-                    const T* xrow = Mc + (size_t)r * LD;
-                    const T* orow = Mo + (size_t)r * LD;
-                    int cnt = 0, chosen = 0x7fffffff;
-#pragma unroll
-                    for (int c = 0; c < CH; ++c) {
-                        const int k = lane + 32 * c;
-                        const T lam = lrow[k] + (orow[k] + xrow[k]);
-                        const bool keep = lam > T(0);
-                        const unsigned bal = __ballot_sync(kFull, keep);
-                        cnt += __popc(bal);
-                        if (bal && chosen == 0x7fffffff) chosen = 32 * c + __ffs(bal) - 1;
-                        if (tr_on && trl && k < s) trl[((size_t)shot * a.s_cap + r) * a.s_cap + k] = lam * (T)kLn2;
-                    }
-                    if (lane == 0) choice[r] = chosen;
-                    ok_all &= (cnt == 1);
-                }
-                const int conv = __syncthreads_and(ok_all);
-                bool have_cand = false, cand_forced = false;
-                if (conv) {
-                    any_conv = true;
-                    have_cand = true;
-                } else if (a.decoder == 1 || t == a.T) {
-                    // ---- forced convergence on lambda^t by locally dominant rounds
-                    forced_ran = true;
-                    for (int r = tid; r < s; r += NTH) matched[r] = 0;
-                    __syncthreads();
-                    for (int round = 0; round < s; ++round) {
-                        for (int r = warp; r < s; r += W) {
-                            if (matched[r]) continue;  // uniform per warp
-                            const T* lrow = Lg + (size_t)r * LD;
-                            const T* xrow = Mc + (size_t)r * LD;
-                            const T* orow = Mo + (size_t)r * LD;
-                            T bl = ninf;
-                            int bk = 0x7fffffff;
-#pragma unroll
-                            for (int c = 0; c < CH; ++c) {
-                                const int k = lane + 32 * c;
-                                if (k < s && (k == r || !matched[k])) {
-                                    const T lam = lrow[k] + (orow[k] + xrow[k]);
-                                    if (bk == 0x7fffffff || lam > bl) {
-                                        bl = lam;
-                                        bk = k;
-                                    }
-                                }
-                            }
-#pragma unroll
-                            for (int off = 16; off; off >>= 1) {
-                                const T ol = __shfl_xor_sync(kFull, bl, off);
-                                const int okk = __shfl_xor_sync(kFull, bk, off);
-                                if (okk != 0x7fffffff && (bk == 0x7fffffff || ol > bl || (ol == bl && okk < bk))) {
-                                    bl = ol;
-                                    bk = okk;
-                                }
-                            }
-                            if (lane == 0) choice[r] = bk != 0x7fffffff ? bk : r;
-                        }
-                        __syncthreads();
-                        int left = 0;
-                        for (int r = tid; r < s; r += NTH) {
-                            if (matched[r]) continue;
-                            const int pk = choice[r];
-                            const bool newm = (pk == r) || (choice[pk] == r);
-                            rowacc[r] = newm ? 1.0 : 0.0;
-                            left += !newm;
-                        }
-                        __syncthreads();
-                        for (int r = tid; r < s; r += NTH)
-                            if (!matched[r] && rowacc[r] != 0.0) matched[r] = 1;
-                        if (tid == 0) acc_fcr += 1;
-                        if (__syncthreads_count(left) == 0) break;
-                    }
-                    if (tid == 0) acc_fc += 1;
-                    have_cand = true;
-                    cand_forced = true;
-                }
-                if (have_cand) {
-                    int pc = 0;
-                    for (int r = tid; r < s; r += NTH) {
-                        const int k = choice[r];
-                        double w = 0.0;
-                        if (k >= r) {
-                            const size_t off = (size_t)dets[r] * n + dets[k];
-                            pc ^= ic.tb.P[off];
-                            if (full) w = ic.tb.W64[off];
-                        }
-                        rowacc[r] = w;
-                    }
-                    const int par = __syncthreads_count(pc) & 1;
-                    bool finish = false;
-                    if (!full) {
-                        out_par = par;
-                        out_forced = cand_forced;
-                        finish = true;
-                    } else {
-                        if (tid == 0) {
-                            double w = 0.0;
-                            for (int r = 0; r < s; ++r) w += rowacc[r];
-                            sh_improve = 0;
-                            sh_use_best = 0;
-                            if (a.decoder == 1 || !cand_forced) {
-                                if (w < sh_best_w) {
-                                    sh_best_w = w;
-                                    sh_best_par = par;
-                                    sh_best_forced = cand_forced;
-                                    sh_improve = 1;
-                                }
-                            } else {
-                                sh_use_best = sh_best_w <= w;
-                            }
-                        }
-                        __syncthreads();
-                        if (sh_improve)
-                            for (int r = tid; r < s; r += NTH) bestp[r] = (short)choice[r];
-                        if (t == a.T || (a.decoder == 0 && cand_forced)) {
-                            finish = true;
-                            if (a.decoder == 0 && cand_forced && !sh_use_best) {
-                                out_par = par;
-                                out_forced = 1;
-                            } else {
-                                out_par = sh_best_par;
-                                out_forced = sh_best_forced;
-                                out_from_best = 1;
-                            }
-                        }
-                        __syncthreads();
-                    }
-                    if (finish) break;
-                }
-                __syncthreads();
-            }
-            // ---- update pass: M' for every row, batch by batch
-            T* Mn = Mtb[cur ^ 1];
-            const int nbatch = (s + W - 1) / W;
-            int ok_w = 1;  // fused decisions: every row of this warp keeps exactly one variable
-            T* const pbuf = pf + warp * 3 * LD;
-            // row rr of Lg, Mc and Mo into this warp's prefetch buffer (one commit group)
-            auto prefetch = [&](int rr) {
-                const T* src[3] = {Lg + (size_t)rr * LD, Mc + (size_t)rr * LD, Mo + (size_t)rr * LD};
-                constexpr int V = LD * (int)sizeof(T) / 16;  // 16-byte chunks per row
-#pragma unroll
-                for (int m = 0; m < 3; ++m)
-                    for (int v = lane; v < V; v += 32) cp_async16(pbuf + m * LD + v * (16 / (int)sizeof(T)),
-                                                                  src[m] + v * (16 / (int)sizeof(T)));
-                cp_async_commit();
-            };
-            if constexpr (PF)
-                if (warp < s) prefetch(warp);
-            for (int b = 0; b < nbatch; ++b) {
-                const int r = b * W + warp;
-                T* srow = stage + warp * SP;
-                if (r < s) {
-                    const T* lrow = Lg + (size_t)r * LD;
-                    const T* xrow = Mc + (size_t)r * LD;
-                    T* orow = Mo + (size_t)r * LD;
-                    T lv[PFM == 1 ? CH : 1], xv[PFM == 1 ? CH : 1], ov[PFM == 1 ? CH : 1];
-                    if constexpr (PF) {
-                        cp_async_wait_all();
-                        __syncwarp();
-                    }
-                    if constexpr (PFM == 1) {
-#pragma unroll
-                        for (int c = 0; c < CH; ++c) {
-                            const int k = lane + 32 * c;
-                            lv[c] = pbuf[k];
-                            xv[c] = pbuf[LD + k];
-                            ov[c] = pbuf[2 * LD + k];
-                        }
-                        __syncwarp();
-                        if (r + W < s) prefetch(r + W);
-                    }
-                    // the row's prior, incoming message and own output at column lane + 32 c
-                    auto LV = [&](int c) -> T {
-                        if constexpr (PFM == 1) return lv[c];
-                        else if constexpr (PFM == 2) return pbuf[lane + 32 * c];
-                        else return lrow[lane + 32 * c];
-                    };
-                    auto XV = [&](int c) -> T {
-                        if constexpr (PFM == 1) return xv[c];
-                        else if constexpr (PFM == 2) return pbuf[LD + lane + 32 * c];
-                        else return xrow[lane + 32 * c];
-                    };
-                    auto OV = [&](int c) -> T {
-                        if constexpr (PFM == 1) return ov[c];
-                        else if constexpr (PFM == 2) return pbuf[2 * LD + lane + 32 * c];
-                        else return orow[lane + 32 * c];
-                    };
-                    if (fuse) {
-                        int cnt = 0, chosen = 0x7fffffff;
-#pragma unroll
-                        for (int c = 0; c < CH; ++c) {
-                            const T lam = LV(c) + (OV(c) + XV(c));
-                            const unsigned bal = __ballot_sync(kFull, lam > T(0));
-                            cnt += __popc(bal);
-                            if (bal && chosen == 0x7fffffff) chosen = 32 * c + __ffs(bal) - 1;
-                        }
-                        if (lane == 0) choice[r] = chosen;
-                        ok_w &= (cnt == 1);
-                    }
-                    T q[CH];
-                    T m1 = ninf, m2 = ninf;
-                    int am = 0x7fffffff;
-#pragma unroll
-                    for (int c = 0; c < CH; ++c) {
-                        const int k = lane + 32 * c;
-                        const T v = B2<T>::fma_(XV(c), ainv, LV(c));
-                        q[c] = v;
-                        const bool gt = v > m1;
-                        m2 = B2<T>::mx(m2, B2<T>::mn(v, m1));
-                        m1 = B2<T>::mx(m1, v);
-                        am = gt ? k : am;
-                    }
-                    if constexpr (PFM == 2) {
-                        // the last read of this row's buffer: the next row may replace it
-                        __syncwarp();
-                        if (r + W < s) prefetch(r + W);
-                    }
-#pragma unroll
-                    for (int off = 16; off; off >>= 1) {
-                        const T o1 = __shfl_xor_sync(kFull, m1, off);
-                        const T o2 = __shfl_xor_sync(kFull, m2, off);
-                        const int ok = __shfl_xor_sync(kFull, am, off);
-                        combine_max(m1, m2, am, o1, o2, ok);
-                    }
-                    T S = T(0);
-#pragma unroll
-                    for (int c = 0; c < CH; ++c) {
-                        const T u = B2<T>::ex2(B2<T>::mn(q[c], m2) - m2);
-                        q[c] = u;
-                        S += u;
-                    }
-                    S = warp_sum(S);
-                    const T cf = B2<T>::ex2(m2 - m1);
-                    const T Aa = B2<T>::fma_(cf, S - T(1), T(1));
-#pragma unroll
-                    for (int c = 0; c < CH; ++c) {
-                        const int k = lane + 32 * c;
-                        const T out = -m1 - B2<T>::lg2(B2<T>::fma_(-cf, q[c], Aa));
-                        orow[k] = out;
-                        srow[k] = out;
-                    }
-                    if ((am & 31) == lane) {
-                        const T oam = -m2 - B2<T>::lg2(S - T(1));
-                        orow[am] = oam;
-                        srow[am] = oam;
-                    }
-                    __syncwarp();
-                    if (lane == 0) srow[r] = T(0);  // the diagonal of Mt stays 0
-                }
-                __syncthreads();
-                // transposed write of the batch: Mn[k][b*W + w] = stage[w][k]
-                const int r0 = b * W;
-                const int rows = min(W, s - r0);
-                for (int e = tid; e < s * W; e += NTH) {
-                    const int k = e / W, w = e % W;
-                    if (w < rows) Mn[(size_t)k * LD + r0 + w] = stage[w * SP + k];
-                }
-                __syncthreads();
-            }
-            if (fuse && __syncthreads_and(ok_w)) {
-                // lambda^t converged: its matching is the output (the update just made is unused)
-                any_conv = true;
-                int pc = 0;
-                for (int r = tid; r < s; r += NTH) {
-                    const int k = choice[r];
-                    if (k >= r) pc ^= ic.tb.P[(size_t)dets[r] * n + dets[k]];
-                }
-                out_par = __syncthreads_count(pc) & 1;
-                out_forced = 0;
-                break;
-            }
-            cur ^= 1;
-            ++t;
-        }
-        if (tr_on && a.tr_partner) {
-            for (int r = tid; r < a.s_cap; r += NTH) {
-                int pk = -1;
-                if (r < s) pk = out_from_best ? (int)bestp[r] : choice[r];
-                a.tr_partner[(size_t)shot * a.s_cap + r] = (int16_t)pk;
-            }
-        }
-        if (tid == 0) {
-            if (ic.obs_pred) ic.obs_pred[shot] = (uint8_t)out_par;
-            if (ic.flags)
-                ic.flags[shot] = (uint8_t)((any_conv ? F_CONVERGED : 0) | (forced_ran ? F_FORCED_RAN : 0) |
-                                          (out_forced ? F_FROM_FORCED : 0));
-            if (ic.iters) ic.iters[shot] = (int16_t)t;
-            acc_it += (unsigned long long)t;
-            acc_msg += (unsigned long long)s * s * t;
-            acc_def += (unsigned long long)s;
-            acc_shots += 1;
-        }
-        __syncthreads();
-    }
-    if (tid == 0 && a.ctr) {
-        atomicAdd(a.ctr + C_ITERS, acc_it);
-        atomicAdd(a.ctr + C_MSGS, acc_msg);
-        atomicAdd(a.ctr + C_DEFECTS, acc_def);
-        atomicAdd(a.ctr + C_TIER_MSGS + a.tier, acc_msg);
-        atomicAdd(a.ctr + C_TIER_SHOTS + a.tier, acc_shots);
-        atomicAdd(a.ctr + C_FC_RUNS, acc_fc);
-        atomicAdd(a.ctr + C_FC_ROUNDS, acc_fcr);
-    }
-}
-
 // ------------------------------------------------------------------ no-allocation scratch
 //
 // bp4m_decode_noalloc serves callers that cannot allocate device memory.  Its scratch is
@@ -881,21 +429,6 @@ cudaError_t launch_decode_noalloc(int precision, DecodeArgs a, int64_t shots, cu
 
 namespace {
 
-template <typename T, int CH>
-cudaError_t run_stream(const DecodeArgs& a, int slots, cudaStream_t st) {
-    constexpr int LD = 32 * CH;
-    constexpr int W = kStreamWarpsOf<T, CH>;
-    const size_t smem = (kStreamPrefetch<T, CH> != 0 ? (size_t)W * 3 * LD * sizeof(T) : 0) +
-                        (size_t)W * (LD + 1) * sizeof(T) + sizeof(T) +
-                        (size_t)LD * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 16;
-    const bool tr = a.tr_lambda != nullptr || a.tr_partner != nullptr;
-    auto kern = tr ? decode_stream_kernel<T, CH, true, W> : decode_stream_kernel<T, CH, false, W>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kern<<<slots, W * 32, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
 // Columns per lane of the streaming kernel for shots of up to max_s defects; 0 when the
 // general global kernel takes them.
 // FP32 steps of 64 columns up to 512 and of 128 columns up to 1024 keep the padding of a
@@ -931,9 +464,11 @@ size_t global_slot_bytes(int precision, int max_s, int* gsmax_out) {
     const size_t esz = precision == 0 ? sizeof(double) : sizeof(float);
     const int ch = stream_ch(precision, max_s);
     if (ch) {
-        const size_t ld = 32 * (size_t)ch;
-        *gsmax_out = (int)ld;
-        return 4 * ld * ld * esz;
+        const int ld = 32 * ch;
+        *gsmax_out = ld;
+        return precision == 0   ? stream_slot_bytes<double, double>(ld)
+               : precision == 1 ? stream_slot_bytes<float, float>(ld)
+                                : stream_slot_bytes<float, __half>(ld);  // 16-bit messages, FP32 priors
     }
     const int gsmax = (max_s + 63) / 64 * 64;
     *gsmax_out = gsmax;
@@ -944,6 +479,7 @@ cudaError_t launch_decode_global(int precision, const DecodeArgs& a, int slots, 
     if (slots <= 0) return cudaSuccess;
     const int ch = stream_ch(precision, a.gsmax);
     if (ch && 32 * ch == a.gsmax) {
+        if (precision >= 2) return launch_stream_half(precision, ch, a, slots, st);
         if (precision == 0) {
             if (ch == 8) return run_stream<double, 8>(a, slots, st);
             return run_stream<double, 16>(a, slots, st);

@@ -227,7 +227,9 @@ def test_every_tier_boundary_d13(torch, prec, early):
 @pytest.mark.parametrize("prec,sizes", [
     ("fp32", [40, 161, 192]), ("fp32", [193, 256]), ("fp32", [120, 257, 320]), ("fp32", [321, 384]),
     ("fp32", [385, 448]), ("fp32", [449, 512]), ("fp32", [513, 600]), ("fp32", [300, 700]), ("fp32", [200, 800]),
-    ("fp32", [100, 900]), ("fp64", [113, 256]), ("fp64", [257, 512])])
+    ("fp32", [100, 900]), ("fp64", [113, 256]), ("fp64", [257, 512]),
+    ("fp16", [40, 161, 192]), ("fp16", [193, 256]), ("fp16", [321, 384]), ("fp16", [513, 600]), ("fp16", [100, 900]),
+    ("bf16", [161, 250]), ("bf16", [300, 700])])
 def test_streaming_tier_every_width(torch, prec, sizes):
     g, og, ot = circuit_pair(13, 0.005)
     sb = _random_syndromes(og.n_det, sizes, seed=sum(sizes))
@@ -236,7 +238,9 @@ def test_streaming_tier_every_width(torch, prec, sizes):
     cap = max(sizes)
     res = gpu_decode(g, synd, T, pkg.make_opts(precision=prec, early_exit=False), s_cap=cap)
     assert list(res["s"]) == sizes
-    rtol = 1e-10 if prec == "fp64" else 1e-4
+    # 16-bit message storage (FP32 priors and arithmetic): the bounds of the shared-memory
+    # tiers' 16-bit test
+    rtol = {"fp64": 1e-10, "fp32": 1e-4, "fp16": 5e-3, "bf16": 4e-2}[prec]
     worst = 0.0
     for k, s in enumerate(sizes):
         dets = np.flatnonzero(sb[k])
@@ -247,7 +251,8 @@ def test_streaming_tier_every_width(torch, prec, sizes):
     print("%s %s: worst |dlambda|/(|l|+1) = %.3g" % (prec, sizes, worst))
     assert worst < rtol
     res = gpu_decode(g, synd, T, pkg.make_opts(precision=prec, early_exit=True), s_cap=cap)
-    tau = TAU64 if prec == "fp64" else TAU32
+    # decisions: the margin rule, with the 16-bit formats' posterior error scale
+    tau = {"fp64": TAU64, "fp32": TAU32, "fp16": 0.2, "bf16": 1.5}[prec]
     cnt, bad = compare_shots(ot, sb, res, T, range(len(sizes)), tau)
     assert all(m < tau for _, m in bad), bad
     assert np.array_equal(res["obs"], res["obs2"]) and np.array_equal(res["flags"] & 1, res["conv"])

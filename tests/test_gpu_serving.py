@@ -133,17 +133,17 @@ def test_rejects_device_buffers_and_bbp4mf(graphs):
 
 
 def test_heavy_request_is_served_in_pieces(graphs):
-    # a 1536-shot request of the d = 25 circuit (a heavy graph, streaming tier) is decoded in
-    # pieces of at most 512 shots; small requests submitted right after it are served
+    # a 3072-shot request of the d = 25 circuit (a heavy graph, streaming tier) is decoded in
+    # pieces of at most 1024 shots; small requests submitted right after it are served
     # between its pieces, and every result equals decode alone
     g_heavy, g_light = graphs[3], graphs[0]
-    heavy = _host_syndromes(g_heavy, 1536, seed=41)
+    heavy = _host_syndromes(g_heavy, 3072, seed=41)
     light = _host_syndromes(g_light, 400, seed=42)
     opts = pkg.make_opts(precision="fp32", early_exit=True)
     srv = pkg.Server(slots=2, max_batch_shots=4096)
     gid_h, gid_l = srv.add_graph(g_heavy), srv.add_graph(g_light)
-    out_h = np.empty(1536, dtype=np.uint8)
-    conv_h = np.empty(1536, dtype=np.uint8)
+    out_h = np.empty(3072, dtype=np.uint8)
+    conv_h = np.empty(3072, dtype=np.uint8)
     rid_h = srv.submit(gid_h, heavy, T, opts, out_h, conv_h)
     small = []
     for k in range(4):
@@ -161,5 +161,5 @@ def test_heavy_request_is_served_in_pieces(graphs):
     # at least three pieces for the heavy request, and the small requests did not wait for
     # all of it
     assert st["batches"] >= 3 + 1
-    assert info_h["batch_shots"] <= 512
+    assert info_h["batch_shots"] <= 1024
     assert min(info["t_done"] for info, _, _ in infos) < info_h["t_done"]
