@@ -89,7 +89,21 @@ typedef struct {
     double alpha;    /* variable-update memory parameter (Sec. "BP Improvements"); 1 = plain */
     int type;        /* code capacity only: 0 = X errors on the Z-check graph,
                         1 = Z errors on the X-check graph.  Ignored for circuits. */
+    int forced;      /* forced convergence (Sec. "Forced convergence"): BP4M_FORCED_GREEDY
+                        (default) or BP4M_FORCED_STATIC */
 } bp4m_opts;
+
+/* Forced convergence orders the variables by posterior and picks a matching.
+   GREEDY: all variables sorted by posterior (descending; ties: smaller i, then smaller j),
+   each accepted iff its factors are unmatched (the global greedy; it reproduces the
+   paper's worked example).  STATIC: the paper's static partition, each pair v_ij (i <= j)
+   in the block of factor c_i; each block's maximum (ties: smaller j) represents its factor,
+   the representatives are processed by posterior (descending; ties: smaller i); a factor
+   not yet matched is matched along its representative (to the boundary for v_ii, else
+   together with the other factor), and to the boundary when the representative's other
+   factor is already matched, a case the paper does not treat. */
+#define BP4M_FORCED_GREEDY 0
+#define BP4M_FORCED_STATIC 1
 
 /* Aggregate counts of one sample_and_decode call (all u64). */
 typedef struct {

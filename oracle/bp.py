@@ -134,6 +134,63 @@ def forced_convergence(lam, valid=None):
     return picks
 
 
+def forced_convergence_static(lam, valid=None):
+    """Forced convergence with the paper's static partition (Sec. "Forced convergence"):
+    the variables are partitioned into one block per factor, v_ij (i <= j) belonging to the
+    block of c_i (the partition of the full detector set, each pair owned by its smaller
+    detector, restricted to the shot); each block's maximum (ties: smaller j) represents its
+    factor; the representatives are ordered by posterior, descending (ties: smaller i), and
+    processed in that order: a factor not yet matched is matched along its representative
+    v_ik, to the boundary if k = i, else together with c_k.  The paper does not say what
+    happens when c_k has already been matched; then c_i is matched to the boundary (always
+    available, so the result is a valid matching).  Returns pairs in pick order."""
+    s = lam.shape[0]
+    if valid is None:
+        valid = full_valid(s)
+    rep = []
+    for i in range(s):
+        best, bj = -math.inf, i
+        for j in range(i, s):
+            if valid[i, j] and (lam[i, j] > best or (bj == i and best == -math.inf)):
+                best, bj = float(lam[i, j]), j
+        rep.append((best, bj))
+    order = sorted(range(s), key=lambda i: (-rep[i][0], i))
+    matched = [False] * s
+    picks = []
+    for i in order:
+        if matched[i]:
+            continue
+        k = rep[i][1]
+        if k == i or matched[k]:
+            picks.append((i, i))
+            matched[i] = True
+        else:
+            picks.append((i, k))
+            matched[i] = matched[k] = True
+    return picks
+
+
+def static_margin(lam, valid=None):
+    """Smallest posterior gap that decides forced_convergence_static: within a block, its
+    maximum against the block's next largest; across blocks, adjacent representatives in
+    the processing order (inf if there are none)."""
+    s = lam.shape[0]
+    if valid is None:
+        valid = full_valid(s)
+    margin = math.inf
+    reps = []
+    for i in range(s):
+        vals = sorted((float(lam[i, j]) for j in range(i, s) if valid[i, j]), reverse=True)
+        if len(vals) >= 2:
+            margin = min(margin, vals[0] - vals[1])
+        if vals:
+            reps.append(vals[0])
+    reps.sort(reverse=True)
+    for a, b in zip(reps, reps[1:]):
+        margin = min(margin, a - b)
+    return margin
+
+
 # Perturbation size up to which decision_margin and the first-stage margin of B-BP4MF check
 # that a decision cannot change: at least the largest tolerance the tests use (1e-2).
 ROBUST_AT = 0.05

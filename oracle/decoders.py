@@ -51,7 +51,15 @@ def candidate_weight(W, matching):
     return acc
 
 
-def bp4m(L, W, T, early_exit=True, alpha=1.0, keep_hist=False):
+def _forced(lam, forced):
+    """(matching in pick order, decisive margin) of forced convergence: the global greedy
+    (default reading) or the paper's static partition."""
+    if forced == "static":
+        return bp.forced_convergence_static(lam), bp.static_margin(lam)
+    return bp.forced_convergence(lam), bp.greedy_margin(lam)
+
+
+def bp4m(L, W, T, early_exit=True, alpha=1.0, keep_hist=False, forced="greedy"):
     """BP4M on one shot's prior matrix L (s x s, diagonal = boundary) and weights W."""
     s = L.shape[0]
     r = ShotResult()
@@ -87,17 +95,17 @@ def bp4m(L, W, T, early_exit=True, alpha=1.0, keep_hist=False):
         r.weight, r.matching = best
         return r
     r.fallback = True
-    r.margin = min(r.margin, bp.greedy_margin(lam))
-    forced = bp.forced_convergence(lam)
-    wf = candidate_weight(W, forced)
+    fmatch, fmargin = _forced(lam, forced)
+    r.margin = min(r.margin, fmargin)
+    wf = candidate_weight(W, fmatch)
     if best is not None and best[0] <= wf:
         r.weight, r.matching = best
     else:
-        r.weight, r.matching, r.from_forced = wf, forced, True
+        r.weight, r.matching, r.from_forced = wf, fmatch, True
     return r
 
 
-def bp4mf(L, W, T, alpha=1.0, keep_hist=False):
+def bp4mf(L, W, T, alpha=1.0, keep_hist=False, forced="greedy"):
     """BP4MF (alpha = 1) and Memory-BP4MF (alpha != 1) on one shot."""
     s = L.shape[0]
     r = ShotResult()
@@ -117,14 +125,15 @@ def bp4mf(L, W, T, alpha=1.0, keep_hist=False):
         V, conv = bp.decide(lam)
         if conv:
             any_conv = True
-            match, forced = bp.matching_from(V), False
+            match, from_forced = bp.matching_from(V), False
         else:
-            r.margin = min(r.margin, bp.greedy_margin(lam))
-            match, forced = bp.forced_convergence(lam), True
+            match, fmargin = _forced(lam, forced)
+            r.margin = min(r.margin, fmargin)
+            from_forced = True
             r.fallback = True
         w = candidate_weight(W, match)
         if best is None or w < best[0]:
-            best = (w, match, forced)
+            best = (w, match, from_forced)
         r.lam = lam
     r.iters = T
     r.lam_hist = hist
@@ -133,15 +142,17 @@ def bp4mf(L, W, T, alpha=1.0, keep_hist=False):
     return r
 
 
-def decode_shot(tables, dets, T, decoder="bp4m", early_exit=True, alpha=1.0, keep_hist=False):
-    """Decode one shot given its sorted unsatisfied detectors; fills obs_pred."""
+def decode_shot(tables, dets, T, decoder="bp4m", early_exit=True, alpha=1.0, keep_hist=False, forced="greedy"):
+    """Decode one shot given its sorted unsatisfied detectors; fills obs_pred.  forced:
+    "greedy" (global greedy forced convergence, the default reading) or "static" (the
+    paper's static partition)."""
     dets = np.asarray(dets, dtype=np.int64)
     L = tables.L[np.ix_(dets, dets)]
     W = tables.W[np.ix_(dets, dets)]
     if decoder == "bp4m":
-        r = bp4m(L, W, T, early_exit=early_exit, alpha=alpha, keep_hist=keep_hist)
+        r = bp4m(L, W, T, early_exit=early_exit, alpha=alpha, keep_hist=keep_hist, forced=forced)
     elif decoder == "bp4mf":
-        r = bp4mf(L, W, T, alpha=alpha, keep_hist=keep_hist)
+        r = bp4mf(L, W, T, alpha=alpha, keep_hist=keep_hist, forced=forced)
     else:
         raise ValueError(decoder)
     par = 0

@@ -59,11 +59,14 @@ def _stream(stream):
     return int(stream)
 
 
-def make_opts(precision=FP32, early_exit=True, decoder="bp4m", alpha=1.0, type=0):
+def make_opts(precision=FP32, early_exit=True, decoder="bp4m", alpha=1.0, type=0, forced="greedy"):
+    """Decoder options (bp4m_opts).  forced: "greedy" (global greedy forced convergence) or
+    "static" (the paper's static partition of the variables into per-factor blocks)."""
     dec = ({"bp4m": DEC_BP4M, "bp4mf": DEC_BP4MF, "bbp4mf": DEC_BBP4MF}[decoder] if isinstance(decoder, str)
            else int(decoder))
     prec = {"fp32": FP32, "fp64": FP64, "fp16": FP16, "bf16": BF16}[precision] if isinstance(precision, str) else int(precision)
-    return _capi.Opts(prec, 1 if early_exit else 0, dec, float(alpha), int(type))
+    fc = {"greedy": 0, "static": 1}[forced] if isinstance(forced, str) else int(forced)
+    return _capi.Opts(prec, 1 if early_exit else 0, dec, float(alpha), int(type), fc)
 
 
 class Graph:

@@ -498,6 +498,8 @@ int check_opts(const bp4m_graph* g, const bp4m_opts* o, int iters) {
     if (iters < 1 || iters > 30000) return fail(BP4M_EINVAL, "iters must be in [1, 30000]");
     if (g->host.n_types == 2 && (o->type < 0 || o->type > 1))
         return fail(BP4M_EINVAL, "type must be 0 (X) or 1 (Z)");
+    if (o->forced != BP4M_FORCED_GREEDY && o->forced != BP4M_FORCED_STATIC)
+        return fail(BP4M_EINVAL, "forced must be BP4M_FORCED_GREEDY or BP4M_FORCED_STATIC");
     return BP4M_OK;
 }
 
@@ -541,6 +543,7 @@ int decode_device(bp4m_graph* g, Workspace& w, int ty, const uint32_t* synd, int
     a.T = T;
     a.early_exit = o->early_exit ? 1 : 0;
     a.decoder = o->decoder;
+    a.forced_static = o->forced == BP4M_FORCED_STATIC ? 1 : 0;
     a.alpha = o->alpha;
     a.obs_pred = obs_pred;
     a.flags = flags;
@@ -929,7 +932,7 @@ struct GateHold {
 bool same_batch(const SrvRequest& a, const SrvRequest& b) {
     return a.graph == b.graph && a.iters == b.iters && a.opts.precision == b.opts.precision &&
            a.opts.early_exit == b.opts.early_exit && a.opts.decoder == b.opts.decoder &&
-           a.opts.alpha == b.opts.alpha && a.opts.type == b.opts.type;
+           a.opts.alpha == b.opts.alpha && a.opts.type == b.opts.type && a.opts.forced == b.opts.forced;
 }
 
 }  // namespace
@@ -1245,6 +1248,7 @@ int multi_enqueue(bp4m_multi* m, const std::vector<int64_t>& shots, int plan) {
     a.T = m->iters;
     a.early_exit = m->opts.early_exit ? 1 : 0;
     a.decoder = m->opts.decoder;
+    a.forced_static = m->opts.forced == BP4M_FORCED_STATIC ? 1 : 0;
     a.alpha = m->opts.alpha;
     a.ctr = m->ctr;
     for (int tier = 1; tier < kGlobalTier; ++tier) {
@@ -1977,6 +1981,7 @@ int bp4m_decode_noalloc(const bp4m_graph* g, const uint32_t* syndromes, int64_t 
     a.T = iters;
     a.early_exit = opts->early_exit ? 1 : 0;
     a.decoder = opts->decoder;
+    a.forced_static = opts->forced == BP4M_FORCED_STATIC ? 1 : 0;
     a.alpha = opts->alpha;
     a.obs_pred = obs_pred;
     a.flags = converged;

@@ -320,6 +320,8 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
     unsigned char* matched = reinterpret_cast<unsigned char*>(bestp + SMAX);
     // 16-bit messages: nrefv[k] = -r_k, minus the reference of the messages leaving factor k
     float* nrefv = reinterpret_cast<float*>(smem + nref_offset<T, MS>(SMAX, G));
+    // static-partition forced convergence: factors in processing order
+    short* order = reinterpret_cast<short*>(smem + nref_offset<T, MS>(SMAX, G) + (HALF ? (size_t)SMAX * 4 : 0));
     // RW only: per-shot W (FP64) and parity over local ranks, Dijkstra state per warp, in
     // this block's global scratch slot (layout of rw_slot_layout)
     const int rw_nodes = a.tb.n_det + 1;
@@ -703,7 +705,72 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                     if (act && g == 0) matched[i] = 0;
                     __syncthreads();
                     const T lii = act ? (REG ? Lm[i * P + i] + (mo.get(c_diag) + T(0)) : Lm[i * P + i] + Dg[i]) : ninf;
-                    for (int round = 0; round < s; ++round) {
+                    if (a.forced_static) {
+                        // the paper's static partition: row i's block is v_ik, k >= i; its
+                        // maximum (ties: smaller k) represents factor i; representatives are
+                        // ranked by posterior (ties: smaller i) and processed in that order
+                        T bl = ninf;
+                        int bk = -1;
+                        if (act) {
+#pragma unroll
+                            for (int c = 0; c < CH; ++c) {
+                                const int k = COL(c);
+                                if (k >= i && k < s) {
+                                    const T own = REG ? mo[REG ? c : 0] : CM(c);
+                                    T lam = RL(c) + (own + RM(c));
+                                    if (!REG && k == i) lam = lii;
+                                    if (REG && k == am_prev) lam = RL(c) + (out_am + RM(c));
+                                    if (bk < 0 || lam > bl) {
+                                        bl = lam;
+                                        bk = k;
+                                    }
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int off = R; off < 32; off <<= 1) {
+                            const T ol = __shfl_xor_sync(kFull, bl, off);
+                            const int ok = __shfl_xor_sync(kFull, bk, off);
+                            if (ok >= 0 && (bk < 0 || ol > bl || (ol == bl && ok < bk))) {
+                                bl = ol;
+                                bk = ok;
+                            }
+                        }
+                        if (act && g == 0) {
+                            choice[i] = bk >= 0 ? bk : i;
+                            rowacc[i] = (double)bl;
+                        }
+                        __syncthreads();
+                        if (tid < s) {
+                            const double v = rowacc[tid];
+                            int rank = 0;
+                            for (int j = 0; j < s; ++j) {
+                                const double u = rowacc[j];
+                                rank += (u > v || (u == v && j < tid)) ? 1 : 0;
+                            }
+                            order[rank] = (short)tid;
+                        }
+                        __syncthreads();
+                        if (tid == 0) {
+                            // a factor whose representative's other factor is taken goes to
+                            // the boundary (a case the paper does not treat)
+                            for (int r = 0; r < s; ++r) {
+                                const int ii = order[r];
+                                if (matched[ii]) continue;
+                                const int k = choice[ii];
+                                matched[ii] = 1;
+                                if (k == ii || matched[k]) {
+                                    choice[ii] = ii;
+                                } else {
+                                    matched[k] = 1;
+                                    choice[k] = ii;
+                                }
+                            }
+                            acc_fcr += 1;
+                        }
+                        __syncthreads();
+                    }
+                    for (int round = 0; round < s && !a.forced_static; ++round) {
                         const bool open = act && !matched[i];
                         T bl = ninf;
                         int bk = -1;
@@ -1046,7 +1113,7 @@ inline int64_t rw_slot_layout(int smax, int nt, int nodes) {
 template <typename T, int CH, int G, typename MS = T>
 size_t smem_bytes_of() {
     constexpr int SMAX = CH * G;
-    return nref_offset<T, MS>(SMAX, G) + (sizeof(MS) == 2 ? (size_t)SMAX * sizeof(float) : 0) + 16;
+    return nref_offset<T, MS>(SMAX, G) + (sizeof(MS) == 2 ? (size_t)SMAX * sizeof(float) : 0) + (size_t)SMAX * 2 + 16;
 }
 
 template <typename T, int CH, int G, bool TRACE, bool REG, typename MS = T>

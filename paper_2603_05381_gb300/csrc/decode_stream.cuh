@@ -105,6 +105,8 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
     unsigned char* matched = reinterpret_cast<unsigned char*>(bestp + LD);
     // 16-bit: nref[b][k] = -r_k of the messages in Mtb[b] and of the own outputs (b = parity)
     float* nref = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(matched + LD + 15) & ~(uintptr_t)15);
+    // static-partition forced convergence: factors in processing order
+    short* order = reinterpret_cast<short*>(nref + (HALF ? 2 * LD : 0));
     __shared__ int sh_item, sh_s, sh_best_par, sh_best_forced, sh_improve, sh_use_best;
     __shared__ double sh_best_w;
 
@@ -218,7 +220,72 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                     forced_ran = true;
                     for (int r = tid; r < s; r += NTH) matched[r] = 0;
                     __syncthreads();
-                    for (int round = 0; round < s; ++round) {
+                    if (a.forced_static) {
+                        // the paper's static partition: row r's block is v_rk, k >= r; its
+                        // maximum (ties: smaller k) represents factor r; representatives are
+                        // ranked by posterior (ties: smaller r) and processed in that order
+                        for (int r = warp; r < s; r += W) {
+                            const T* lrow = Lg + (size_t)r * LD;
+                            const MS* xrow = Mc + (size_t)r * LD;
+                            const MS* orow = Mo + (size_t)r * LD;
+                            T bl = ninf;
+                            int bk = 0x7fffffff;
+#pragma unroll
+                            for (int c = 0; c < CH; ++c) {
+                                const int k = lane + 32 * c;
+                                if (k >= r && k < s) {
+                                    const T lam = lrow[k] + (down(orow + k, r) + dx(xrow + k, k));
+                                    if (bk == 0x7fffffff || lam > bl) {
+                                        bl = lam;
+                                        bk = k;
+                                    }
+                                }
+                            }
+#pragma unroll
+                            for (int off = 16; off; off >>= 1) {
+                                const T ol = __shfl_xor_sync(kFull, bl, off);
+                                const int okk = __shfl_xor_sync(kFull, bk, off);
+                                if (okk != 0x7fffffff && (bk == 0x7fffffff || ol > bl || (ol == bl && okk < bk))) {
+                                    bl = ol;
+                                    bk = okk;
+                                }
+                            }
+                            if (lane == 0) {
+                                choice[r] = bk != 0x7fffffff ? bk : r;
+                                rowacc[r] = (double)bl;
+                            }
+                        }
+                        __syncthreads();
+                        for (int r = tid; r < s; r += NTH) {
+                            const double v = rowacc[r];
+                            int rank = 0;
+                            for (int j = 0; j < s; ++j) {
+                                const double u = rowacc[j];
+                                rank += (u > v || (u == v && j < r)) ? 1 : 0;
+                            }
+                            order[rank] = (short)r;
+                        }
+                        __syncthreads();
+                        if (tid == 0) {
+                            // a factor whose representative's other factor is taken goes to the
+                            // boundary (a case the paper does not treat)
+                            for (int q = 0; q < s; ++q) {
+                                const int rr = order[q];
+                                if (matched[rr]) continue;
+                                const int k = choice[rr];
+                                matched[rr] = 1;
+                                if (k == rr || matched[k]) {
+                                    choice[rr] = rr;
+                                } else {
+                                    matched[k] = 1;
+                                    choice[k] = rr;
+                                }
+                            }
+                            acc_fcr += 1;
+                        }
+                        __syncthreads();
+                    }
+                    for (int round = 0; round < s && !a.forced_static; ++round) {
                         for (int r = warp; r < s; r += W) {
                             if (matched[r]) continue;  // uniform per warp
                             const T* lrow = Lg + (size_t)r * LD;
@@ -532,8 +599,8 @@ size_t stream_smem_bytes() {
     constexpr int LD = 32 * CH;
     constexpr int W = kStreamWarpsOf<T, CH>;
     return (kStreamPrefetch<T, CH> != 0 ? (size_t)W * 3 * LD * sizeof(T) : 0) + (size_t)W * (LD + 1) * sizeof(T) +
-           sizeof(T) + (size_t)LD * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 16 +
-           (sizeof(MS) == 2 ? (size_t)2 * LD * sizeof(float) + 16 : 0);
+           sizeof(T) + (size_t)LD * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 32 +
+           (sizeof(MS) == 2 ? (size_t)2 * LD * sizeof(float) : 0) + (size_t)LD * sizeof(short);
 }
 
 template <typename T, int CH, typename MS = T>

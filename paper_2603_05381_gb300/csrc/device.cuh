@@ -77,6 +77,7 @@ struct DecodeArgs {
     int T = 0;
     int early_exit = 1;
     int decoder = 0;                 // 0 = BP4M, 1 = BP4MF
+    int forced_static = 0;           // forced convergence: 0 = global greedy, 1 = static partition
     double alpha = 1.0;
     int pitch = 0;                   // shared-memory row pitch in elements
     int tier = 0;                    // decode tier (per-tier counters)

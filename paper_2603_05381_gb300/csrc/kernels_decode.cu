@@ -32,6 +32,8 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
     int* choice = dets + gsmax;
     short* bestp = reinterpret_cast<short*>(choice + gsmax);
     unsigned char* matched = reinterpret_cast<unsigned char*>(bestp + gsmax);
+    // static-partition forced convergence: factors in processing order
+    short* order = reinterpret_cast<short*>(reinterpret_cast<uintptr_t>(matched + gsmax + 1) & ~(uintptr_t)1);
     __shared__ int sh_item, sh_s, sh_best_par, sh_best_forced, sh_improve, sh_use_best;
     __shared__ double sh_best_w;
     T* slot = reinterpret_cast<T*>(a.gscratch) + (size_t)blockIdx.x * 3 * a.gslot_elems;
@@ -140,7 +142,56 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
                     forced_ran = true;
                     for (int r = tid; r < s; r += kGlobThreads) matched[r] = 0;
                     __syncthreads();
-                    for (int round = 0; round < s; ++round) {
+                    if (a.forced_static) {
+                        // the paper's static partition: row r's block is v_rk, k >= r; its
+                        // maximum (ties: smaller k) represents factor r; representatives are
+                        // ranked by posterior (ties: smaller r) and processed in that order
+                        for (int r = tid; r < s; r += kGlobThreads) {
+                            T bl = Num<T>::ninf();
+                            int bk = -1;
+                            for (int k = r; k < s; ++k) {
+                                const T l = Lg[(size_t)r * s + k];
+                                const T own = Mc[(size_t)k * s + r];
+                                const T lam = (k == r) ? l + own : l + (own + Mc[(size_t)r * s + k]);
+                                if (bk < 0 || lam > bl) {
+                                    bl = lam;
+                                    bk = k;
+                                }
+                            }
+                            choice[r] = bk >= 0 ? bk : r;
+                            rowacc[r] = (double)bl;
+                        }
+                        __syncthreads();
+                        for (int r = tid; r < s; r += kGlobThreads) {
+                            const double v = rowacc[r];
+                            int rank = 0;
+                            for (int j = 0; j < s; ++j) {
+                                const double u = rowacc[j];
+                                rank += (u > v || (u == v && j < r)) ? 1 : 0;
+                            }
+                            order[rank] = (short)r;
+                        }
+                        __syncthreads();
+                        if (tid == 0) {
+                            // a factor whose representative's other factor is taken goes to the
+                            // boundary (a case the paper does not treat)
+                            for (int q = 0; q < s; ++q) {
+                                const int rr = order[q];
+                                if (matched[rr]) continue;
+                                const int k = choice[rr];
+                                matched[rr] = 1;
+                                if (k == rr || matched[k]) {
+                                    choice[rr] = rr;
+                                } else {
+                                    matched[k] = 1;
+                                    choice[k] = rr;
+                                }
+                            }
+                            acc_fcr += 1;
+                        }
+                        __syncthreads();
+                    }
+                    for (int round = 0; round < s && !a.forced_static; ++round) {
                         for (int r = tid; r < s; r += kGlobThreads) {
                             if (matched[r]) continue;
                             T bl = Num<T>::ninf();
@@ -305,6 +356,11 @@ __global__ void __launch_bounds__(kGlobThreads) decode_global_kernel(const Decod
     }
 }
 
+// Dynamic shared memory of the general global-memory kernel for shots of up to gsmax defects.
+inline size_t global_kernel_smem(int gsmax) {
+    return (size_t)gsmax * (sizeof(double) + 2 * sizeof(int) + 2 * sizeof(short) + 1) + 32;
+}
+
 // ------------------------------------------------------------------ no-allocation scratch
 //
 // bp4m_decode_noalloc serves callers that cannot allocate device memory.  Its scratch is
@@ -408,7 +464,7 @@ cudaError_t launch_decode_noalloc(int precision, DecodeArgs a, int64_t shots, cu
     a.gscratch = b + kNoAllocHeader;
     a.gslot_elems = (int64_t)kNoAllocSlotElems;
     a.gsmax = kNoAllocMaxDefects;
-    const size_t smem = (size_t)a.gsmax * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 16;
+    const size_t smem = global_kernel_smem(a.gsmax);
     if (precision == 0)
         decode_global_kernel<double><<<kNoAllocSlots, kGlobThreads, smem, st>>>(a);
     else
@@ -497,7 +553,7 @@ cudaError_t launch_decode_global(int precision, const DecodeArgs& a, int slots, 
             default: return run_stream<float, 32>(a, slots, st);
         }
     }
-    const size_t smem = (size_t)a.gsmax * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 16;
+    const size_t smem = global_kernel_smem(a.gsmax);
     cudaError_t e;
     if (precision == 0) {
         e = cudaFuncSetAttribute(decode_global_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

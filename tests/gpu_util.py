@@ -69,7 +69,7 @@ def oracle_partner(matching, s):
 
 
 def compare_shots(tables, synd_bool, gpu, T, idx, tau, decoder="bp4m", early_exit=True, alpha=1.0,
-                  check_partner=True, pool=None, oracle=None):
+                  check_partner=True, pool=None, oracle=None, forced="greedy"):
     """Decodes shots `idx` with the oracle (in this process, or over `pool`, an
     oracle_pool.OraclePool of the same tables) and compares with the GPU.  Returns
     (n_compared, list of mismatching (shot, margin)).  `oracle`, if given, holds the oracle's
@@ -80,7 +80,7 @@ def compare_shots(tables, synd_bool, gpu, T, idx, tau, decoder="bp4m", early_exi
         results = [oracle[k] for k in idx]
     elif pool is not None:
         results = pool.decode([np.flatnonzero(synd_bool[k]) for k in idx], T, decoder=decoder,
-                              early_exit=early_exit, alpha=alpha)
+                              early_exit=early_exit, alpha=alpha, forced=forced)
     else:
         results = None
     bad = []
@@ -89,7 +89,7 @@ def compare_shots(tables, synd_bool, gpu, T, idx, tau, decoder="bp4m", early_exi
         if results is not None:
             r = results[pos]
         else:
-            r = decode_shot(tables, dets, T, decoder=decoder, early_exit=early_exit, alpha=alpha)
+            r = decode_shot(tables, dets, T, decoder=decoder, early_exit=early_exit, alpha=alpha, forced=forced)
         same = (r.obs_pred == int(gpu["obs"][k]) and int(r.converged) == int(gpu["flags"][k] & 1)
                 and r.iters == int(gpu["iters"][k]) and int(r.from_forced) == int((gpu["flags"][k] >> 2) & 1))
         if same and check_partner and "partner" in gpu and len(dets) <= gpu["partner"].shape[1] and len(dets):

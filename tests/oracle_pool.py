@@ -18,9 +18,9 @@ def _init(L, W, P):
 
 def _decode(task):
     from oracle.decoders import decode_shot
-    dets, T, decoder, early_exit, alpha = task
+    dets, T, decoder, early_exit, alpha, forced = task
     r = decode_shot(_TB["tb"], np.asarray(dets, dtype=np.int64), T, decoder=decoder, early_exit=early_exit,
-                    alpha=alpha)
+                    alpha=alpha, forced=forced)
     return (int(r.obs_pred), bool(r.converged), int(r.iters), bool(r.from_forced),
             [(int(i), int(j)) for i, j in r.matching], float(r.margin))
 
@@ -41,8 +41,8 @@ class OraclePool:
         self.pool = ctx.Pool(self.procs, initializer=_init,
                              initargs=(np.asarray(tables.L), np.asarray(tables.W), np.asarray(tables.P)))
 
-    def decode(self, dets_list, T, decoder="bp4m", early_exit=True, alpha=1.0):
-        tasks = [(np.asarray(d, dtype=np.int64), T, decoder, early_exit, alpha) for d in dets_list]
+    def decode(self, dets_list, T, decoder="bp4m", early_exit=True, alpha=1.0, forced="greedy"):
+        tasks = [(np.asarray(d, dtype=np.int64), T, decoder, early_exit, alpha, forced) for d in dets_list]
         # large shots first so that the pool's tail is short
         order = sorted(range(len(tasks)), key=lambda k: -len(tasks[k][0]))
         out = self.pool.map(_decode, [tasks[k] for k in order], chunksize=1)

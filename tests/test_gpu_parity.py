@@ -443,3 +443,38 @@ def test_bbp4mf_matches_oracle(torch, prec, d, p, n):
     assert not bad, bad[:5]
     # the rule has teeth: most shots are not exempt
     assert exempt <= n // 4
+
+
+# ------------------------------------------------------------------ static-partition forced convergence
+
+
+@pytest.mark.parametrize("prec,decoder,early", [("fp64", "bp4m", False), ("fp64", "bp4mf", False),
+                                                 ("fp32", "bp4m", True), ("fp32", "bp4mf", False)])
+def test_static_partition_forced_convergence(torch, prec, decoder, early):
+    # the paper's static partition of the variables into per-factor blocks, as an option:
+    # sampled d = 5 shots, and random d = 13 syndromes across the shared-memory tiers and the
+    # streaming tier, against the oracle with the same option (matchings compared)
+    tau = TAU64 if prec == "fp64" else TAU32
+    opts = pkg.make_opts(precision=prec, early_exit=early, decoder=decoder, forced="static")
+    g, og, ot = circuit_pair(5, 0.008)
+    n, T = 300, 20
+    (synd,), _ = gpu_sample(g, 0, n, seed=23)
+    res = gpu_decode(g, synd, T, opts, s_cap=64)
+    cnt, bad = compare_shots(ot, as_bool(synd, og.n_det), res, T, range(n), tau, decoder=decoder, early_exit=early,
+                             forced="static")
+    assert all(m < tau for _, m in bad), bad[:5]
+    assert len(bad) <= cnt // 50
+    g, og, ot = circuit_pair(13, 0.005)
+    sizes = [2, 40, 70, 100, 120, 140, 155, 170, 230, 300]
+    if prec == "fp64":
+        sizes.append(600)  # the general global-memory kernel (above the FP64 streaming widths)
+    sb = _random_syndromes(og.n_det, sizes, seed=29)
+    synd = torch.as_tensor(pack_syndromes(sb).view(np.int32), device="cuda")
+    T = 5
+    res = gpu_decode(g, synd, T, opts, s_cap=max(sizes))
+    cnt, bad = compare_shots(ot, sb, res, T, range(len(sizes)), tau, decoder=decoder, early_exit=early, forced="static")
+    assert all(m < tau for _, m in bad), bad
+    # the production kernels agree with the traced ones, and the option changes outputs
+    assert np.array_equal(res["obs"], res["obs2"])
+    greedy = gpu_decode(g, synd, T, pkg.make_opts(precision=prec, early_exit=early, decoder=decoder), s_cap=max(sizes))
+    assert not np.array_equal(greedy["partner"], res["partner"])

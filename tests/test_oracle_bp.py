@@ -223,3 +223,45 @@ def test_decision_margin_is_sound(seed):
         assert c == c0
         if c0:
             assert np.array_equal(V, V0)
+
+
+def test_worked_example_static_partition():
+    # the paper's static partition (each pair in the block of its smaller factor) reproduces
+    # the worked example's pick order too: block maxima v14 (c1), v22 (c2), v33 (c3), v44
+    # (c4); c1 takes c4 along v14, then c3 and c2 go to the boundary
+    ex = json.load(open(GOLDEN))
+    s = ex["s"]
+    lam = np.full((s, s), -np.inf)
+    for key, pv in ex["prob_v1"].items():
+        i, j = (int(x) - 1 for x in key.split(","))
+        lam[i, j] = lam[j, i] = math.log(pv / (1 - pv))
+    picks = bp.forced_convergence_static(lam)
+    assert [(i + 1, j + 1) for (i, j) in picks] == [tuple(x) for x in ex["forced_pick_order"]]
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_static_partition_gives_a_valid_matching_and_sound_margin(seed):
+    rng = np.random.default_rng(300 + seed)
+    s = 3 + seed
+    lam = _random_lambda(s, rng, ties=False)
+    picks = bp.forced_convergence_static(lam)
+    covered = sorted(x for i, j in picks for x in ({i, j}))
+    assert covered == list(range(s))           # every factor matched exactly once
+    # each pick is its factor's block maximum, or the boundary when that partner was taken
+    for i, j in picks:
+        blk = [lam[i, k] for k in range(i, s)]
+        assert j == i or lam[i, j] == max(blk)
+    m = bp.static_margin(lam)
+    for _ in range(200):
+        d = rng.uniform(-1, 1, size=(s, s)) * 0.49 * m
+        assert sorted(bp.forced_convergence_static(_perturb(lam, d))) == sorted(picks)
+
+
+def test_static_partition_equals_greedy_without_conflicts():
+    # when every factor's block maximum leads to an unmatched partner in processing order,
+    # both readings pick the same variables (a diagonal-dominant case)
+    s = 5
+    lam = np.full((s, s), -5.0)
+    for i in range(s):
+        lam[i, i] = 1.0 + i
+    assert sorted(bp.forced_convergence_static(lam)) == sorted(bp.forced_convergence(lam))
