@@ -75,8 +75,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     # fused multi-graph decode of circuit and code-capacity graphs (d = 5, 9, 13, 17) with
     # uneven shot counts, FP16/BF16/FP32 messages against the plain per-graph FP32 form
-    ap.add_argument("--fused", action="store_true")
-    ap.add_argument("--fused-scale", type=float, default=1.0)
+    ap.add_argument("--fused", default=True, action=argparse.BooleanOptionalAction)
+    ap.add_argument("--fused-scale", type=float, default=0.1)
     # only measure the special-function unit (the shared-memory tiers' roofline
     # denominator) with the SM clocks sampled meanwhile, print it and exit
     ap.add_argument("--mufu-probe", action="store_true")

@@ -53,6 +53,19 @@ constexpr int kStreamWarpsOf = sizeof(T) != 4 ? kStreamWarps : (CH >= 10 && CH <
 template <typename T, int CH>
 constexpr int kStreamPrefetch = sizeof(T) != 4 ? 0 : CH <= 8 ? 1 : 2;
 
+// Dynamic shared memory of one streaming block with `stages` output stages.
+template <typename T, int CH, typename MS>
+constexpr size_t stream_smem_bytes_n(int stages) {
+    return (kStreamPrefetch<T, CH> != 0 ? (size_t)kStreamWarpsOf<T, CH> * 3 * (32 * CH) * sizeof(T) : 0) +
+           (size_t)stages * kStreamWarpsOf<T, CH> * (32 * CH + 1) * sizeof(T) + sizeof(T) +
+           (size_t)(32 * CH) * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 32 +
+           (sizeof(MS) == 2 ? (size_t)2 * (32 * CH) * sizeof(float) : 0) + (size_t)(32 * CH) * sizeof(short);
+}
+// Two output stages where they fit: 227 KB per block, and for the two-block variants 113 KB.
+template <typename T, int CH, typename MS>
+constexpr int kStreamStages =
+    stream_smem_bytes_n<T, CH, MS>(2) <= (kStreamWarpsOf<T, CH> == kStreamWarps && kStreamBlocks<T, CH> == 2 ? 113u : 227u) * 1024u ? 2 : 1;
+
 // 16-byte asynchronous global->shared copies (cp.async, L2 only), used to fetch a warp's next
 // factor row while it works on the current one
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
@@ -97,8 +110,11 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
     constexpr bool PF = PFM != 0;
     extern __shared__ __align__(16) unsigned char smem[];
     T* const pf = reinterpret_cast<T*>(smem);
-    T* stage = pf + (PF ? W * 3 * LD : 0);                          // [W][SP]
-    double* rowacc = reinterpret_cast<double*>(stage + W * SP + ((W * SP) & 1));
+    // output stage [NST][W][SP]: with two stages a batch's rows go to one while the previous
+    // batch's transposed write reads the other, one block barrier per batch instead of two
+    constexpr int NST = kStreamStages<T, CH, MS>;
+    T* stage0 = pf + (PF ? W * 3 * LD : 0);
+    double* rowacc = reinterpret_cast<double*>(stage0 + NST * W * SP + ((NST * W * SP) & 1));
     int* dets = reinterpret_cast<int*>(rowacc + LD);
     int* choice = dets + LD;
     short* bestp = reinterpret_cast<short*>(choice + LD);
@@ -415,6 +431,7 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                 if (warp < s) prefetch(warp);
             for (int b = 0; b < nbatch; ++b) {
                 const int r = b * W + warp;
+                T* const stage = stage0 + (NST == 2 ? (b & 1) : 0) * W * SP;
                 T* srow = stage + warp * SP;
                 if (r < s) {
                     const T* lrow = Lg + (size_t)r * LD;
@@ -544,8 +561,12 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                     const int k = e / W, w = e % W;
                     if (w < rows) Mn[(size_t)k * LD + r0 + w] = MS(stage[w * SP + k]);
                 }
-                __syncthreads();
+                // one stage: the next batch may overwrite it only after this write; two stages:
+                // the next batch writes the other one, and the barrier after its rows (which
+                // every thread reaches only after this write) protects this one
+                if (NST == 1) __syncthreads();
             }
+            if (NST == 2) __syncthreads();  // the last batch's transposed write precedes every read of Mn
             if (fuse && __syncthreads_and(ok_w)) {
                 // lambda^t converged: its matching is the output (the update just made is unused)
                 any_conv = true;
@@ -596,11 +617,7 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
 // Dynamic shared memory of one streaming block.
 template <typename T, int CH, typename MS>
 size_t stream_smem_bytes() {
-    constexpr int LD = 32 * CH;
-    constexpr int W = kStreamWarpsOf<T, CH>;
-    return (kStreamPrefetch<T, CH> != 0 ? (size_t)W * 3 * LD * sizeof(T) : 0) + (size_t)W * (LD + 1) * sizeof(T) +
-           sizeof(T) + (size_t)LD * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 32 +
-           (sizeof(MS) == 2 ? (size_t)2 * LD * sizeof(float) : 0) + (size_t)LD * sizeof(short);
+    return stream_smem_bytes_n<T, CH, MS>(kStreamStages<T, CH, MS>);
 }
 
 template <typename T, int CH, typename MS = T>
