@@ -553,9 +553,24 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
 
         for (;;) {
             // ---- read phase: Q = l + M[k][i]/alpha for the next update; for t > 0 the
-            // marginalization of lambda^t = l + (M[i][k] + M[k][i])
+            // marginalization of lambda^t = l + (M[i][k] + M[k][i]).  FP32: the row's
+            // maximum / second maximum scan of the next update runs in the same loop (it needs
+            // only Q), so that the shared-memory loads and the scan's ALU work overlap; the
+            // scan is over columns in the same order as a separate pass, so its result is the
+            // same
             Mask bits = 0;
             float cntf = 0.f;
+            float sa1 = Num<float>::ninf(), sa2 = Num<float>::ninf();
+            int sac = 0x7fffffff;
+            auto scan_pair = [&](int j, float v, float w) {
+                // (max, second max, column) of the pairs so far; ties to the smaller column
+                const float hi = fmaxf(v, w), lo = fminf(v, w);
+                const int ih = v >= w ? 2 * j : 2 * j + 1;
+                const bool gt = hi > sa1;
+                sa2 = max3f(sa2, lo, fminf(sa1, hi));
+                sa1 = fmaxf(sa1, hi);
+                sac = gt ? ih : sac;
+            };
             if (!wact) {
             } else if (!act) {
 #pragma unroll
@@ -565,8 +580,10 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                     if constexpr (std::is_same<T, float>::value) {
                         const float2 ainv2 = make_float2(ainv, ainv);
 #pragma unroll
-                        for (int j = 0; j < CH / 2; ++j)
+                        for (int j = 0; j < CH / 2; ++j) {
                             q.p[j] = __ffma2_rn(RM2(j), ainv2, RL2(j));
+                            scan_pair(j, q.p[j].x, q.p[j].y);
+                        }
                     } else {
 #pragma unroll
                         for (int c = 0; c < CH; ++c) q[c] = B2<T>::fma_(RM(c), ainv, RL(c));
@@ -589,6 +606,7 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                         else
                             own = make_float2(CM(c), CM(c + 1));
                         q.p[j] = __ffma2_rn(x, ainv2, l);
+                        scan_pair(j, q.p[j].x, q.p[j].y);
                         const float2 lam = __fadd2_rn(l, __fadd2_rn(own, x));
                         cnt2 = __fadd2_rn(cnt2, make_float2(keep_f(lam.x), keep_f(lam.y)));
                         if (tr_on && trl && COL(c) < s)
@@ -640,6 +658,23 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                         const T lam = Lm[i * P + am_prev] + (out_am + m_ld1(Mt + i * PM + am_prev, am_prev));
                         bits = (bits & ~((Mask)1 << ca)) | ((Mask)(lam > T(0) ? 1u : 0u) << ca);
                         if (tr_on && trl) trl[((size_t)shot * a.s_cap + i) * a.s_cap + am_prev] = lam * (T)kLn2;
+                    }
+                }
+            }
+            // FP32: the row's (m1, m2, argmax column) of the next update, over the G threads
+            T m1 = ninf, m2 = ninf;
+            int am = 0x7fffffff;
+            if constexpr (std::is_same<T, float>::value) {
+                if (wact) {
+                    m1 = sa1;
+                    m2 = sa2;
+                    am = sac < CH ? COL(sac) : 0x7fffffff;
+#pragma unroll
+                    for (int off = R; off < 32; off <<= 1) {
+                        const T o1 = __shfl_xor_sync(kFull, m1, off);
+                        const T o2 = __shfl_xor_sync(kFull, m2, off);
+                        const int ok = __shfl_xor_sync(kFull, am, off);
+                        combine_max(m1, m2, am, o1, o2, ok);
                     }
                 }
             }
@@ -884,27 +919,86 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
             // (the max clamped to m2, so S - 1 = sum_{k != am} 2^(Q_k - m2) >= 1):
             //   k != am: M'[i][k] = -(m1 + lg2(1 + 2^(m2 - m1) (S - 1 - 2^(Q_k - m2))))
             //   k == am: M'[i][k] = -(m2 + lg2(S - 1))
+            // (the generic value is written for every column, the owner of am then overwrites;
+            // row i's outputs M'[i][k] go to Mt[k][i]).  FP32: (m1, m2, am) come from the read
+            // phase; FP64: from the scan below.
             if (wact) {
-                T m1, m2;
-                int am;
                 if constexpr (std::is_same<T, float>::value) {
-                    // column pairs: hi/lo of the pair, then the running (max, second max);
-                    // ties go to the smaller column
-                    float a1 = ninf, a2 = ninf;
-                    int ac = 0x7fffffff;
+                    const float2 nm2 = make_float2(-m2, -m2);
+                    float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int j = 0; j < CH / 2; ++j) {
-                        const float v = q.p[j].x, w = q.p[j].y;
-                        const float hi = fmaxf(v, w), lo = fminf(v, w);
-                        const int ih = v >= w ? 2 * j : 2 * j + 1;
-                        const bool gt = hi > a1;
-                        a2 = max3f(a2, lo, fminf(a1, hi));
-                        a1 = fmaxf(a1, hi);
-                        ac = gt ? ih : ac;
+                        const float2 dq = __fadd2_rn(make_float2(fminf(q.p[j].x, m2), fminf(q.p[j].y, m2)), nm2);
+                        const float2 u = make_float2(B2<float>::ex2(dq.x), B2<float>::ex2(dq.y));
+                        q.p[j] = u;
+                        s2 = __fadd2_rn(s2, u);
                     }
-                    m1 = a1;
-                    m2 = a2;
-                    am = ac < CH ? COL(ac) : 0x7fffffff;
+                    float S32 = s2.x + s2.y;
+#pragma unroll
+                    for (int off = R; off < 32; off <<= 1) S32 += __shfl_xor_sync(kFull, S32, off);
+                    const float cf32 = B2<float>::ex2(m2 - m1);
+                    const float Aa32 = __fmaf_rn(cf32, S32 - 1.f, 1.f);
+                    // 16-bit storage: this row's reference r_i = m1 rounded to the format (so
+                    // that it is exact there); stored values out + r_i = -lg2(Aa - cf u) + (r_i - m1)
+                    float rf32 = 0.f, dref32 = 0.f;
+                    if constexpr (HALF) {
+                        rf32 = IO::unpack(IO::pack(m1, 0.f)).x;
+                        dref32 = rf32 - m1;
+                    }
+                    if (act) {
+                        const float rf = rf32;
+                        // out = -m1 - lg2(Aa - cf u), the subtraction as an exact fma with -1
+                        const float2 ncf = make_float2(-cf32, -cf32), A2 = make_float2(Aa32, Aa32);
+                        const float2 nm1 = HALF ? make_float2(dref32, dref32) : make_float2(-m1, -m1);
+                        const float2 neg1 = make_float2(-1.f, -1.f);
+#pragma unroll
+                        for (int j = 0; j < CH / 2; ++j) {
+                            const float2 y = __ffma2_rn(ncf, q.p[j], A2);
+                            const float2 lg = make_float2(B2<float>::lg2(y.x), B2<float>::lg2(y.y));
+                            const float2 out = __ffma2_rn(lg, neg1, nm1);
+                            if constexpr (HALF) {
+                                // store the rounded pair (relative to r_i); the register copy is
+                                // the stored value decoded as every reader decodes it, so that
+                                // both ends of a variable see the same message
+                                const unsigned pk2 = IO::pack(out.x, out.y);
+                                *reinterpret_cast<unsigned short*>(CMP(2 * j)) = (unsigned short)(pk2 & 0xFFFFu);
+                                *reinterpret_cast<unsigned short*>(CMP(2 * j + 1)) = (unsigned short)(pk2 >> 16);
+                                if constexpr (REG) mo.p[j] = __fadd2_rn(IO::unpack(pk2), make_float2(-rf, -rf));
+                            } else {
+                                *CMP(2 * j) = out.x;
+                                *CMP(2 * j + 1) = out.y;
+                                if constexpr (REG) mo.p[j] = out;
+                            }
+                        }
+                        float oam = -m2 - B2<float>::lg2(S32 - 1.f);
+                        if constexpr (HALF) {
+                            const float st_am = __fmaf_rn(B2<float>::lg2(S32 - 1.f), -1.f, rf - m2);
+                            if (owner_of<PAIR, G>(am) == g) IO::st(Mt + am * PM + i, st_am);
+                            oam = IO::unpack(IO::pack(st_am, 0.f)).x + (-rf);
+                        } else if (owner_of<PAIR, G>(am) == g) {
+                            IO::st(Mt + am * PM + i, oam);
+                        }
+                        if (REG) {
+                            am_prev = am;
+                            out_am = oam;
+                            // what the packed output loop produced for the argmax column: u = ex2(0)
+                            const float u0 = B2<float>::ex2(0.f);
+                            float og = __fmaf_rn(B2<float>::lg2(__fmaf_rn(-cf32, u0, Aa32)), -1.f, HALF ? dref32 : -m1);
+                            if constexpr (HALF) og = IO::unpack(IO::pack(og, 0.f)).x + (-rf);
+                            out_am_gen = og;
+                        }
+                        if (own_diag) {
+                            if constexpr (HALF) {
+                                // the diagonal holds r_i, which decodes to exactly 0
+                                if (!REG) Dg[i] = IO::ld(Mt + i * PM + i) + (-rf);
+                                IO::st(Mt + i * PM + i, rf);
+                                nrefv[i] = -rf;
+                            } else {
+                                if (!REG) Dg[i] = IO::ld(Mt + i * PM + i);
+                                Mt[i * PM + i] = MS(0.f);
+                            }
+                        }
+                    }
                 } else {
                     T a1 = ninf, a2 = ninf, b1 = ninf, b2 = ninf;
                     int ac = 0x7fffffff, bc = 0x7fffffff;
@@ -930,14 +1024,13 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                     m1 = a1;
                     m2 = a2;
                     am = ka;
-                }
 #pragma unroll
-                for (int off = R; off < 32; off <<= 1) {
-                    const T o1 = __shfl_xor_sync(kFull, m1, off);
-                    const T o2 = __shfl_xor_sync(kFull, m2, off);
-                    const int ok = __shfl_xor_sync(kFull, am, off);
-                    combine_max(m1, m2, am, o1, o2, ok);
-                }
+                    for (int off = R; off < 32; off <<= 1) {
+                        const T o1 = __shfl_xor_sync(kFull, m1, off);
+                        const T o2 = __shfl_xor_sync(kFull, m2, off);
+                        const int ok = __shfl_xor_sync(kFull, am, off);
+                        combine_max(m1, m2, am, o1, o2, ok);
+                    }
                 T S;
                 if constexpr (std::is_same<T, float>::value) {
                     const float2 nm2 = make_float2(-m2, -m2);
@@ -1039,6 +1132,7 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                             Mt[i * PM + i] = MS(0.f);
                         }
                     }
+                }
                 }
             }
             __syncthreads();
