@@ -69,9 +69,10 @@ typedef struct {
 #define BP4M_FP64 0
 #define BP4M_FP32 1
 /* 16-bit message storage with FP32 priors and arithmetic: messages are rounded to nearest
-   (saturating at the largest finite value) when stored and read back exactly.  Shared-
-   memory tiers only; shots with more than 160 unsatisfied detectors use FP32 messages.
-   Not for B-BP4MF or bp4m_decode_noalloc (BP4M_EUNSUPPORTED). */
+   (saturating at the largest finite value), relative to a per-row reference, when stored and
+   read back exactly.  Shared-memory and streaming tiers (up to 1024 unsatisfied detectors);
+   the general kernel above them uses FP32 messages.  Not for B-BP4MF or
+   bp4m_decode_noalloc (BP4M_EUNSUPPORTED). */
 #define BP4M_FP16 2
 #define BP4M_BF16 3
 
@@ -91,6 +92,15 @@ typedef struct {
                         1 = Z errors on the X-check graph.  Ignored for circuits. */
     int forced;      /* forced convergence (Sec. "Forced convergence"): BP4M_FORCED_GREEDY
                         (default) or BP4M_FORCED_STATIC */
+    int stream_cluster; /* streaming tier (shots above the shared-memory tiers, FP32 or 16-bit
+                        messages): the thread blocks of a cluster that share one shot.
+                        0 (default): one block per shot when a width class has enough shots
+                        to fill half the device, else the size that finishes the class
+                        soonest (a few heavy shots then run on up to 16 SMs each; the fused
+                        multi-graph decode keeps one block per shot); 1: one block per shot;
+                        2, 4, 8, 16: that size where the width has it and the device can hold
+                        such clusters, else the width's default.  The outputs do not depend
+                        on it. */
 } bp4m_opts;
 
 /* Forced convergence orders the variables by posterior and picks a matching.

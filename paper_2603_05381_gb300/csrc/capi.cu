@@ -500,6 +500,9 @@ int check_opts(const bp4m_graph* g, const bp4m_opts* o, int iters) {
         return fail(BP4M_EINVAL, "type must be 0 (X) or 1 (Z)");
     if (o->forced != BP4M_FORCED_GREEDY && o->forced != BP4M_FORCED_STATIC)
         return fail(BP4M_EINVAL, "forced must be BP4M_FORCED_GREEDY or BP4M_FORCED_STATIC");
+    if (o->stream_cluster != 0 && o->stream_cluster != 1 && o->stream_cluster != 2 && o->stream_cluster != 4 &&
+        o->stream_cluster != 8 && o->stream_cluster != 16)
+        return fail(BP4M_EINVAL, "stream_cluster must be 0, 1, 2, 4, 8 or 16");
     return BP4M_OK;
 }
 
@@ -544,6 +547,7 @@ int decode_device(bp4m_graph* g, Workspace& w, int ty, const uint32_t* synd, int
     a.early_exit = o->early_exit ? 1 : 0;
     a.decoder = o->decoder;
     a.forced_static = o->forced == BP4M_FORCED_STATIC ? 1 : 0;
+    a.stream_cl = o->stream_cluster;
     a.alpha = o->alpha;
     a.obs_pred = obs_pred;
     a.flags = flags;
@@ -623,6 +627,7 @@ int decode_device(bp4m_graph* g, Workspace& w, int ty, const uint32_t* synd, int
         a.tier = kGlobalTier;
         ProfScope ps(g, PROF_GLOBAL, st);
         if (p.gc.n == 1) {
+            a.stream_cl = stream_cluster_for(pio, p.gsmax[0], o->stream_cluster, n_glob, p.full[0]);
             rc = launch_global_classes(a, p, pio, n_glob, w.sub, w.subctr, shots, w.small + kTiers + kGlobalTier,
                                        g->num_sms, st);
             if (rc) return rc;
@@ -652,6 +657,7 @@ int decode_device(bp4m_graph* g, Workspace& w, int ty, const uint32_t* synd, int
                     b.next = w.subctr + kMaxGlobalClasses + c;
                     b.gslot_elems = (int64_t)(p.slot_bytes[c] / esz / 3);
                     b.gsmax = p.gsmax[c];
+                    b.stream_cl = stream_cluster_for(pio, b.gsmax, o->stream_cluster, cnt, p.full[c]);
                     if (small) b.gscratch = static_cast<unsigned char*>(w.gscratch) + p.need;
                     CK(launch_decode_global(pio, b, small ? cnt : std::min(cnt, p.full[c]), small ? w.aux : st));
                 }
@@ -932,7 +938,8 @@ struct GateHold {
 bool same_batch(const SrvRequest& a, const SrvRequest& b) {
     return a.graph == b.graph && a.iters == b.iters && a.opts.precision == b.opts.precision &&
            a.opts.early_exit == b.opts.early_exit && a.opts.decoder == b.opts.decoder &&
-           a.opts.alpha == b.opts.alpha && a.opts.type == b.opts.type && a.opts.forced == b.opts.forced;
+           a.opts.alpha == b.opts.alpha && a.opts.type == b.opts.type && a.opts.forced == b.opts.forced &&
+           a.opts.stream_cluster == b.opts.stream_cluster;
 }
 
 }  // namespace
@@ -1249,6 +1256,7 @@ int multi_enqueue(bp4m_multi* m, const std::vector<int64_t>& shots, int plan) {
     a.early_exit = m->opts.early_exit ? 1 : 0;
     a.decoder = m->opts.decoder;
     a.forced_static = m->opts.forced == BP4M_FORCED_STATIC ? 1 : 0;
+    a.stream_cl = m->opts.stream_cluster;
     a.alpha = m->opts.alpha;
     a.ctr = m->ctr;
     for (int tier = 1; tier < kGlobalTier; ++tier) {
@@ -1982,6 +1990,7 @@ int bp4m_decode_noalloc(const bp4m_graph* g, const uint32_t* syndromes, int64_t 
     a.early_exit = opts->early_exit ? 1 : 0;
     a.decoder = opts->decoder;
     a.forced_static = opts->forced == BP4M_FORCED_STATIC ? 1 : 0;
+    a.stream_cl = opts->stream_cluster;
     a.alpha = opts->alpha;
     a.obs_pred = obs_pred;
     a.flags = converged;

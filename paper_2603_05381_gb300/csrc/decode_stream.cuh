@@ -5,8 +5,10 @@
 // storage ones (kernels_half.cu).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "decode_smem.cuh"
@@ -14,6 +16,8 @@
 
 namespace bp4m {
 namespace {
+
+namespace cg = cooperative_groups;
 
 // ------------------------------------------------------------------ streaming tier
 //
@@ -33,17 +37,32 @@ namespace {
 // memory and writes W consecutive elements per column k.  Iteration = decision pass
 // (lambda of the previous update, convergence vote, candidates / forced convergence), then
 // the update pass.
+//
+// Cluster form (CL > 1, FP32 arithmetic): the CL blocks of a thread-block cluster share one
+// shot and one slot, so that the slots of all shots in flight (one per cluster instead of
+// one per block) stay resident in L2 instead of streaming from HBM every iteration.  Block
+// q of the cluster owns the batches b = q, q + CL, ... (rows b W .. b W + W - 1): it
+// initialises their rows, updates them and takes their decisions.  Messages cross blocks
+// only through the slot (read with L1-bypassing loads); the small per-row state (choices,
+// the 16-bit references, the static partition's block maxima) is written by the row's owner
+// into every block's copy through distributed shared memory, after which every block runs
+// the row-global steps (parity, candidate weights, forced-convergence matching) itself on
+// identical data.  So every value a branch or loop bound depends on is the same in all
+// blocks of a cluster, and every cluster barrier is reached by all of them.
 constexpr int kStreamWarps = 16;
 // Blocks per SM: the 256-column variant (shots of up to 256 defects) runs two, so that one
-// block's L2 latency overlaps the other's arithmetic.
-template <typename T, int CH>
-constexpr int kStreamBlocks = (sizeof(T) == 4 && CH <= 8) ? 2 : 1;
+// block's L2 latency overlaps the other's arithmetic.  The cluster form (CL > 1) runs one
+// 16-warp block per SM at these widths: its slots are L2-resident, and 128 registers per
+// thread keep its rows' registers from spilling.
+template <typename T, int CH, int CL = 1>
+constexpr int kStreamBlocks = (sizeof(T) == 4 && CH <= 8 && CL == 1) ? 2 : 1;
 // Warps per block (one row in flight per warp, each with a 3-row prefetch buffer in shared
 // memory): FP32 320 and 384 columns run one 32-warp block per SM (twice the rows in flight
-// per batch and half the batch barriers of 16 warps), 896 and 1024 columns one 12-warp block
-// (the largest count whose prefetch buffers and output stage fit in 227 KB), the others 16.
-template <typename T, int CH>
-constexpr int kStreamWarpsOf = sizeof(T) != 4 ? kStreamWarps : (CH >= 10 && CH <= 12) ? 32 : CH >= 28 ? 12 : kStreamWarps;
+// per batch and half the batch barriers of 16 warps; 16 in the cluster form), 896 and 1024
+// columns one 12-warp block (the largest count whose prefetch buffers and output stage fit
+// in 227 KB), the others 16.
+template <typename T, int CH, int CL = 1>
+constexpr int kStreamWarpsOf = sizeof(T) != 4 ? kStreamWarps : CH >= 28 ? 12 : (CH >= 10 && CH <= 12 && CL == 1) ? 32 : kStreamWarps;
 // Row prefetch of the update pass: each warp copies its next row of Lg, Mc and Mo into
 // shared memory (asynchronous copies) while it updates the current one.
 //   1: the row is moved into registers and the next copy issued at once (FP32, <= 256 columns)
@@ -54,17 +73,17 @@ template <typename T, int CH>
 constexpr int kStreamPrefetch = sizeof(T) != 4 ? 0 : CH <= 8 ? 1 : 2;
 
 // Dynamic shared memory of one streaming block with `stages` output stages.
-template <typename T, int CH, typename MS>
+template <typename T, int CH, typename MS, int CL = 1>
 constexpr size_t stream_smem_bytes_n(int stages) {
-    return (kStreamPrefetch<T, CH> != 0 ? (size_t)kStreamWarpsOf<T, CH> * 3 * (32 * CH) * sizeof(T) : 0) +
-           (size_t)stages * kStreamWarpsOf<T, CH> * (32 * CH + 1) * sizeof(T) + sizeof(T) +
+    return (kStreamPrefetch<T, CH> != 0 ? (size_t)kStreamWarpsOf<T, CH, CL> * 3 * (32 * CH) * sizeof(T) : 0) +
+           (size_t)stages * kStreamWarpsOf<T, CH, CL> * (32 * CH + 1) * sizeof(T) + sizeof(T) +
            (size_t)(32 * CH) * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 32 +
            (sizeof(MS) == 2 ? (size_t)2 * (32 * CH) * sizeof(float) : 0) + (size_t)(32 * CH) * sizeof(short);
 }
 // Two output stages where they fit: 227 KB per block, and for the two-block variants 113 KB.
-template <typename T, int CH, typename MS>
+template <typename T, int CH, typename MS, int CL = 1>
 constexpr int kStreamStages =
-    stream_smem_bytes_n<T, CH, MS>(2) <= (kStreamWarpsOf<T, CH> == kStreamWarps && kStreamBlocks<T, CH> == 2 ? 113u : 227u) * 1024u ? 2 : 1;
+    stream_smem_bytes_n<T, CH, MS, CL>(2) <= (kStreamBlocks<T, CH, CL> == 2 ? 113u : 227u) * 1024u ? 2 : 1;
 
 // 16-byte asynchronous global->shared copies (cp.async, L2 only), used to fetch a warp's next
 // factor row while it works on the current one
@@ -96,10 +115,11 @@ __host__ __device__ constexpr size_t stream_slot_bytes(int ld) {
     return (size_t)ld * ld * (sizeof(T) + 3 * sizeof(MS));
 }
 
-template <typename T, int CH, bool TRACE, int W, typename MS = T>
-__global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, CH> : 1) decode_stream_kernel(const DecodeArgs a) {
+template <typename T, int CH, bool TRACE, int W, typename MS = T, int CL = 1>
+__global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, CH, CL> : 1) decode_stream_kernel(const DecodeArgs a) {
     constexpr bool HALF = sizeof(MS) == 2;
     static_assert(!HALF || sizeof(T) == 4, "16-bit messages use FP32 arithmetic");
+    static_assert(CL == 1 || (sizeof(T) == 4 && !TRACE && CL <= 16), "cluster form: FP32 arithmetic, no trace");
     using IO = MsgIO<MS, T>;
     constexpr int NTH = W * 32;
     constexpr int LD = 32 * CH;
@@ -112,7 +132,7 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
     T* const pf = reinterpret_cast<T*>(smem);
     // output stage [NST][W][SP]: with two stages a batch's rows go to one while the previous
     // batch's transposed write reads the other, one block barrier per batch instead of two
-    constexpr int NST = kStreamStages<T, CH, MS>;
+    constexpr int NST = kStreamStages<T, CH, MS, CL>;
     T* stage0 = pf + (PF ? W * 3 * LD : 0);
     double* rowacc = reinterpret_cast<double*>(stage0 + NST * W * SP + ((NST * W * SP) & 1));
     int* dets = reinterpret_cast<int*>(rowacc + LD);
@@ -123,11 +143,30 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
     float* nref = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(matched + LD + 15) & ~(uintptr_t)15);
     // static-partition forced convergence: factors in processing order
     short* order = reinterpret_cast<short*>(nref + (HALF ? 2 * LD : 0));
-    __shared__ int sh_item, sh_s, sh_best_par, sh_best_forced, sh_improve, sh_use_best;
+    __shared__ int sh_item2[2], sh_s, sh_best_par, sh_best_forced, sh_improve, sh_use_best;
+    __shared__ int sh_votes[2][CL];  // cluster form: each block's vote, by iteration parity
     __shared__ double sh_best_w;
 
+    // cluster form: this block's rank; writes of per-row state go to every block's copy
+    const int crank = CL > 1 ? (int)cg::this_cluster().block_rank() : 0;
+    auto csync = [&]() {
+        if constexpr (CL > 1)
+            cg::this_cluster().sync();
+        else
+            __syncthreads();
+    };
+    auto bcast = [&](auto* p, auto v) {
+        if constexpr (CL > 1) {
+            cg::cluster_group cl = cg::this_cluster();
+#pragma unroll
+            for (int q = 0; q < CL; ++q) *cl.map_shared_rank(p, q) = v;
+        } else {
+            *p = v;
+        }
+    };
+
     const size_t mat = (size_t)LD * LD;
-    unsigned char* slot = reinterpret_cast<unsigned char*>(a.gscratch) + (size_t)blockIdx.x * stream_slot_bytes<T, MS>(LD);
+    unsigned char* slot = reinterpret_cast<unsigned char*>(a.gscratch) + (size_t)(blockIdx.x / CL) * stream_slot_bytes<T, MS>(LD);
     T* Lg = reinterpret_cast<T*>(slot);
     MS* Mtb[2] = {reinterpret_cast<MS*>(slot + mat * sizeof(T)), reinterpret_cast<MS*>(slot + mat * (sizeof(T) + sizeof(MS)))};
     MS* Mo = reinterpret_cast<MS*>(slot + mat * (sizeof(T) + 2 * sizeof(MS)));
@@ -140,10 +179,18 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
     const T ninf = Num<T>::ninf();
     unsigned long long acc_it = 0, acc_msg = 0, acc_def = 0, acc_shots = 0, acc_fc = 0, acc_fcr = 0;
 
-    for (;;) {
-        if (tid == 0) sh_item = atomicAdd(a.next, 1);
-        __syncthreads();
-        const int item = sh_item;
+    // rows this block owns: r = crank W + warp + j W CL (all rows when CL = 1)
+    const int row0 = crank * W + warp;
+    constexpr int RSTEP = W * CL;
+    // every block of the cluster runs before any block writes into another's shared memory
+    if constexpr (CL > 1) csync();
+    for (int fetch = 0;; ++fetch) {
+        // the cluster's next shot, taken by block 0 and written into every block (two
+        // buffers by fetch parity: a block may still be reading the previous one)
+        const int fb = CL > 1 ? (fetch & 1) : 0;
+        if (crank == 0 && tid == 0) bcast(&sh_item2[fb], atomicAdd(a.next, 1));
+        csync();
+        const int item = sh_item2[fb];
         if (item >= count) break;
         const ItemCtx ic = resolve_item(a, a.list ? (int64_t)a.list[item] : (int64_t)item);
         const int64_t shot = ic.shot;
@@ -156,11 +203,11 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
         __syncthreads();
         const int s = sh_s;
         if (s > LD || s < 2) {
-            if (tid == 0 && a.ctr) atomicAdd(a.ctr + C_ERRORS, 1ull);
+            if (crank == 0 && tid == 0 && a.ctr) atomicAdd(a.ctr + C_ERRORS, 1ull);
             continue;
         }
         const bool tr_on = TRACE && s <= a.s_cap;
-        for (int r = warp; r < s; r += W) {
+        for (int r = row0; r < s; r += RSTEP) {
             const T* trow = Ltab + (size_t)dets[r] * n;
             for (int k = lane; k < LD; k += 32) {
                 Lg[(size_t)r * LD + k] = k < s ? (T)(__ldg(trow + dets[k]) * (T)kLog2e) : ninf;
@@ -180,7 +227,8 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
             sh_best_forced = 0;
             sh_use_best = 0;
         }
-        __syncthreads();
+        // every block's rows of the slot are initialised before any block writes into them
+        csync();
 
         int cur = 0;
         int t = 0;
@@ -200,6 +248,16 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                 if constexpr (HALF) return IO::ld(p) + nrc[k];
                 else return *p;
             };
+            // the same from the slot in global memory (cluster form: rows of Mc are written by
+            // every block of the cluster, so they are read from L2, bypassing this SM's L1)
+            auto dxg = [&](const MS* p, int k) -> T {
+                if constexpr (CL > 1) {
+                    if constexpr (HALF) return IO::unpack((unsigned)__ldcg(reinterpret_cast<const unsigned short*>(p))).x + nrc[k];
+                    else return __ldcg(p);
+                } else {
+                    return dx(p, k);
+                }
+            };
             auto down = [&](const MS* p, int r) -> T {
                 if constexpr (HALF) return IO::ld(p) + nrc[r];
                 else return *p;
@@ -208,7 +266,7 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
             if (t > 0 && !fuse) {
                 // ---- decisions of lambda^t = l + (M[r][k] + M[k][r])
                 int ok_all = 1;
-                for (int r = warp; r < s; r += W) {
+                for (int r = row0; r < s; r += RSTEP) {
                     const T* lrow = Lg + (size_t)r * LD;
                     const MS* xrow = Mc + (size_t)r * LD;
                     const MS* orow = Mo + (size_t)r * LD;
@@ -216,17 +274,27 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
 #pragma unroll
                     for (int c = 0; c < CH; ++c) {
                         const int k = lane + 32 * c;
-                        const T lam = lrow[k] + (down(orow + k, r) + dx(xrow + k, k));
+                        const T lam = lrow[k] + (down(orow + k, r) + dxg(xrow + k, k));
                         const bool keep = lam > T(0);
                         const unsigned bal = __ballot_sync(kFull, keep);
                         cnt += __popc(bal);
                         if (bal && chosen == 0x7fffffff) chosen = 32 * c + __ffs(bal) - 1;
                         if (tr_on && trl && k < s) trl[((size_t)shot * a.s_cap + r) * a.s_cap + k] = lam * (T)kLn2;
                     }
-                    if (lane == 0) choice[r] = chosen;
+                    if (lane == 0) bcast(&choice[r], chosen);
                     ok_all &= (cnt == 1);
                 }
-                const int conv = __syncthreads_and(ok_all);
+                int conv;
+                if constexpr (CL > 1) {
+                    const int cta_ok = __syncthreads_and(ok_all);
+                    if (tid == 0) bcast(&sh_votes[t & 1][crank], cta_ok);
+                    csync();
+                    conv = 1;
+#pragma unroll
+                    for (int q = 0; q < CL; ++q) conv &= sh_votes[t & 1][q];
+                } else {
+                    conv = __syncthreads_and(ok_all);
+                }
                 bool have_cand = false, cand_forced = false;
                 if (conv) {
                     any_conv = true;
@@ -240,7 +308,7 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                         // the paper's static partition: row r's block is v_rk, k >= r; its
                         // maximum (ties: smaller k) represents factor r; representatives are
                         // ranked by posterior (ties: smaller r) and processed in that order
-                        for (int r = warp; r < s; r += W) {
+                        for (int r = row0; r < s; r += RSTEP) {
                             const T* lrow = Lg + (size_t)r * LD;
                             const MS* xrow = Mc + (size_t)r * LD;
                             const MS* orow = Mo + (size_t)r * LD;
@@ -250,7 +318,7 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                             for (int c = 0; c < CH; ++c) {
                                 const int k = lane + 32 * c;
                                 if (k >= r && k < s) {
-                                    const T lam = lrow[k] + (down(orow + k, r) + dx(xrow + k, k));
+                                    const T lam = lrow[k] + (down(orow + k, r) + dxg(xrow + k, k));
                                     if (bk == 0x7fffffff || lam > bl) {
                                         bl = lam;
                                         bk = k;
@@ -267,11 +335,11 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                                 }
                             }
                             if (lane == 0) {
-                                choice[r] = bk != 0x7fffffff ? bk : r;
-                                rowacc[r] = (double)bl;
+                                bcast(&choice[r], bk != 0x7fffffff ? bk : r);
+                                bcast(&rowacc[r], (double)bl);
                             }
                         }
-                        __syncthreads();
+                        csync();
                         for (int r = tid; r < s; r += NTH) {
                             const double v = rowacc[r];
                             int rank = 0;
@@ -297,12 +365,12 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                                     choice[k] = rr;
                                 }
                             }
-                            acc_fcr += 1;
+                            if (crank == 0) acc_fcr += 1;
                         }
                         __syncthreads();
                     }
                     for (int round = 0; round < s && !a.forced_static; ++round) {
-                        for (int r = warp; r < s; r += W) {
+                        for (int r = row0; r < s; r += RSTEP) {
                             if (matched[r]) continue;  // uniform per warp
                             const T* lrow = Lg + (size_t)r * LD;
                             const MS* xrow = Mc + (size_t)r * LD;
@@ -313,7 +381,7 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                             for (int c = 0; c < CH; ++c) {
                                 const int k = lane + 32 * c;
                                 if (k < s && (k == r || !matched[k])) {
-                                    const T lam = lrow[k] + (down(orow + k, r) + dx(xrow + k, k));
+                                    const T lam = lrow[k] + (down(orow + k, r) + dxg(xrow + k, k));
                                     if (bk == 0x7fffffff || lam > bl) {
                                         bl = lam;
                                         bk = k;
@@ -329,9 +397,9 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                                     bk = okk;
                                 }
                             }
-                            if (lane == 0) choice[r] = bk != 0x7fffffff ? bk : r;
+                            if (lane == 0) bcast(&choice[r], bk != 0x7fffffff ? bk : r);
                         }
-                        __syncthreads();
+                        csync();
                         int left = 0;
                         for (int r = tid; r < s; r += NTH) {
                             if (matched[r]) continue;
@@ -343,10 +411,13 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                         __syncthreads();
                         for (int r = tid; r < s; r += NTH)
                             if (!matched[r] && rowacc[r] != 0.0) matched[r] = 1;
-                        if (tid == 0) acc_fcr += 1;
-                        if (__syncthreads_count(left) == 0) break;
+                        if (tid == 0 && crank == 0) acc_fcr += 1;
+                        const int left_all = __syncthreads_count(left);
+                        // cluster form: the next round's choices overwrite every block's copy
+                        if constexpr (CL > 1) csync();
+                        if (left_all == 0) break;
                     }
-                    if (tid == 0) acc_fc += 1;
+                    if (tid == 0 && crank == 0) acc_fc += 1;
                     have_cand = true;
                     cand_forced = true;
                 }
@@ -428,10 +499,11 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
             const MS* pbx = reinterpret_cast<const MS*>(pbuf + LD);
             const MS* pbo = reinterpret_cast<const MS*>(pbuf + 2 * LD);
             if constexpr (PF)
-                if (warp < s) prefetch(warp);
-            for (int b = 0; b < nbatch; ++b) {
+                if (row0 < s) prefetch(row0);
+            // this block's batches b = crank, crank + CL, ...; the stage alternates with b / CL
+            for (int b = crank; b < nbatch; b += CL) {
                 const int r = b * W + warp;
-                T* const stage = stage0 + (NST == 2 ? (b & 1) : 0) * W * SP;
+                T* const stage = stage0 + (NST == 2 ? ((b / CL) & 1) : 0) * W * SP;
                 T* srow = stage + warp * SP;
                 if (r < s) {
                     const T* lrow = Lg + (size_t)r * LD;
@@ -451,7 +523,7 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                             ov[c] = down(pbo + k, r);
                         }
                         __syncwarp();
-                        if (r + W < s) prefetch(r + W);
+                        if (r + RSTEP < s) prefetch(r + RSTEP);
                     }
                     // the row's prior, incoming message and own output at column lane + 32 c
                     auto LV = [&](int c) -> T {
@@ -478,7 +550,7 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                             cnt += __popc(bal);
                             if (bal && chosen == 0x7fffffff) chosen = 32 * c + __ffs(bal) - 1;
                         }
-                        if (lane == 0) choice[r] = chosen;
+                        if (lane == 0) bcast(&choice[r], chosen);
                         ok_w &= (cnt == 1);
                     }
                     T q[CH];
@@ -497,7 +569,7 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                     if constexpr (PFM == 2) {
                         // the last read of this row's buffer: the next row may replace it
                         __syncwarp();
-                        if (r + W < s) prefetch(r + W);
+                        if (r + RSTEP < s) prefetch(r + RSTEP);
                     }
 #pragma unroll
                     for (int off = 16; off; off >>= 1) {
@@ -534,7 +606,7 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                         __syncwarp();
                         if (lane == 0) {
                             srow[r] = rf;  // the diagonal of Mt holds r_r, which decodes to 0
-                            nrn[r] = -rf;
+                            bcast(&nrn[r], -rf);
                         }
                     } else {
 #pragma unroll
@@ -566,8 +638,23 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                 // every thread reaches only after this write) protects this one
                 if (NST == 1) __syncthreads();
             }
-            if (NST == 2) __syncthreads();  // the last batch's transposed write precedes every read of Mn
-            if (fuse && __syncthreads_and(ok_w)) {
+            int fconv;
+            if constexpr (CL > 1) {
+                // every block's transposed writes, choices and references precede every read
+                // of the next iteration
+                if (fuse) {
+                    const int cta_ok = __syncthreads_and(ok_w);
+                    if (tid == 0) bcast(&sh_votes[t & 1][crank], cta_ok);
+                }
+                csync();
+                fconv = fuse;
+#pragma unroll
+                for (int q = 0; q < CL; ++q) fconv &= sh_votes[t & 1][q];
+            } else {
+                if (NST == 2) __syncthreads();  // the last batch's transposed write precedes every read of Mn
+                fconv = fuse && __syncthreads_and(ok_w);
+            }
+            if (fconv) {
                 // lambda^t converged: its matching is the output (the update just made is unused)
                 any_conv = true;
                 int pc = 0;
@@ -589,7 +676,7 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                 a.tr_partner[(size_t)shot * a.s_cap + r] = (int16_t)pk;
             }
         }
-        if (tid == 0) {
+        if (tid == 0 && crank == 0) {
             if (ic.obs_pred) ic.obs_pred[shot] = (uint8_t)out_par;
             if (ic.flags)
                 ic.flags[shot] = (uint8_t)((any_conv ? F_CONVERGED : 0) | (forced_ran ? F_FORCED_RAN : 0) |
@@ -602,7 +689,7 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
         }
         __syncthreads();
     }
-    if (tid == 0 && a.ctr) {
+    if (tid == 0 && crank == 0 && a.ctr) {
         atomicAdd(a.ctr + C_ITERS, acc_it);
         atomicAdd(a.ctr + C_MSGS, acc_msg);
         atomicAdd(a.ctr + C_DEFECTS, acc_def);
@@ -615,9 +702,9 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
 
 
 // Dynamic shared memory of one streaming block.
-template <typename T, int CH, typename MS>
+template <typename T, int CH, typename MS, int CL = 1>
 size_t stream_smem_bytes() {
-    return stream_smem_bytes_n<T, CH, MS>(kStreamStages<T, CH, MS>);
+    return stream_smem_bytes_n<T, CH, MS, CL>(kStreamStages<T, CH, MS, CL>);
 }
 
 template <typename T, int CH, typename MS = T>
@@ -630,6 +717,71 @@ cudaError_t run_stream(const DecodeArgs& a, int slots, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     kern<<<slots, W * 32, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+// Cluster form: the largest number of clusters of CL blocks that can be resident at once
+// on the current device (0 if none), cached per device.
+template <typename T, int CH, typename MS, int CL>
+int stream_cluster_capacity() {
+    static_assert(CL > 1, "cluster form");
+    constexpr int kDev = 16;
+    static std::atomic<int> cache[kDev] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 0;
+    if (dev < kDev) {
+        const int v = cache[dev].load();
+        if (v > 0) return v - 1;
+    }
+    constexpr int W = kStreamWarpsOf<T, CH, CL>;
+    const size_t smem = stream_smem_bytes<T, CH, MS, CL>();
+    auto kern = decode_stream_kernel<T, CH, false, W, MS, CL>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (CL > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(W * 32);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        n = 0;
+    }
+    if (dev < kDev) cache[dev].store(n + 1);
+    return n;
+}
+
+// Launches min(slots, capacity) clusters of CL blocks; the caller's scratch holds `slots`
+// slots of stream_slot_bytes (one per cluster).
+template <typename T, int CH, typename MS, int CL>
+cudaError_t run_stream_cluster(const DecodeArgs& a, int slots, cudaStream_t st) {
+    const int cap = stream_cluster_capacity<T, CH, MS, CL>();
+    if (cap <= 0) return cudaErrorInvalidConfiguration;
+    const int clusters = slots < cap ? slots : cap;
+    if (clusters <= 0) return cudaSuccess;
+    constexpr int W = kStreamWarpsOf<T, CH, CL>;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(clusters * CL));
+    cfg.blockDim = dim3(W * 32);
+    cfg.dynamicSmemBytes = stream_smem_bytes<T, CH, MS, CL>();
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, decode_stream_kernel<T, CH, false, W, MS, CL>, a);
 }
 
 }  // namespace

@@ -113,6 +113,7 @@ struct DecodeArgs {
     int64_t gscratch_bytes = 0;      // size of gscratch (checked by the reweighting launches)
     int64_t gslot_elems = 0;         // elements per slot for each of the three matrices
     int gsmax = 0;                   // largest s a slot holds
+    int stream_cl = 0;               // streaming tier's cluster size (stream_cluster_for); 0 or 1: none
 };
 
 #ifdef __CUDACC__
@@ -242,6 +243,24 @@ cudaError_t launch_decode_global(int precision, const DecodeArgs& a, int slots,
 // Streaming tier with 16-bit message storage (precision 2 = IEEE half, 3 = bfloat16) for
 // ch columns per lane (kernels_half.cu).
 cudaError_t launch_stream_half(int precision, int ch, const DecodeArgs& a, int slots, cudaStream_t st);
+// Cluster form of the streaming tier (kernels_cluster.cu, kernels_cluster_half.cu): the
+// blocks of a thread-block cluster share one shot and one slot.  stream_cluster_size() is the
+// cluster size a launch of ch columns per lane uses (1: one block per shot) for a requested
+// size (0: the default of the width); launch_stream_cluster() runs min(slots, resident
+// clusters) clusters, one slot of the width's size each.
+int stream_cluster_default(int ch);
+bool stream_cluster_instantiated(int precision, int ch, int cl);
+int stream_cluster_capacity_of(int precision, int ch, int cl);
+int stream_cluster_capacity_half(int precision, int ch, int cl);
+int stream_cluster_size(int precision, int ch, int requested);
+// Cluster size for a streaming launch of a class of `shots` shots at slot width gsmax:
+// `requested` if non-zero (as stream_cluster_size), else 1 when the class fills at least half
+// of full_blocks (the resident blocks of one block per shot), else the size that finishes
+// the class soonest.  1 for the general kernel's widths and FP64.
+int stream_cluster_for(int precision, int gsmax, int requested, int64_t shots, int full_blocks);
+cudaError_t launch_stream_cluster(int precision, int ch, int cl, const DecodeArgs& a, int slots, cudaStream_t st);
+cudaError_t launch_stream_cluster_half(int precision, int ch, int cl, const DecodeArgs& a, int slots,
+                                       cudaStream_t st);
 // Width classes of the global tier for a batch whose largest defect count is max_s: class k
 // takes the shots with smax[k-1] < s <= smax[k] (smax ascending; the last class is max_s's
 // own, the general kernel's when max_s is above the widest streaming variant).

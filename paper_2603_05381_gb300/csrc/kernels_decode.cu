@@ -511,6 +511,29 @@ int stream_ch(int precision, int max_s) {
 
 }  // namespace
 
+int stream_cluster_for(int precision, int gsmax, int requested, int64_t shots, int full_blocks) {
+    const int ch = stream_ch(precision, gsmax);
+    if (precision == 0 || ch == 0 || 32 * ch != gsmax) return 1;
+    if (requested != 0) return stream_cluster_size(precision, ch, requested);
+    // automatic: one block per shot while the class fills the device at least half; below
+    // that, the size that finishes the class soonest, with the cluster form's measured cost
+    // per shot and SM of about 1.25 + 0.03 CL times one block's
+    if (shots <= 0 || 2 * shots >= full_blocks) return 1;
+    double best = 1.0;
+    int best_cl = 1;
+    for (int cl : {2, 4, 8, 16}) {
+        const int cap = stream_cluster_capacity_of(precision, ch, cl);
+        if (cap <= 0) continue;
+        const int64_t rounds = (shots + cap - 1) / cap;
+        const double t = (double)rounds * (1.25 + 0.03 * cl) / cl;
+        if (t < best) {
+            best = t;
+            best_cl = cl;
+        }
+    }
+    return best_cl;
+}
+
 int global_blocks_per_sm(int precision, int max_s) {
     const int ch = stream_ch(precision, max_s);
     return (precision != 0 && ch != 0 && ch <= 8) ? kStreamBlocks<float, 8> : 1;
@@ -535,6 +558,11 @@ cudaError_t launch_decode_global(int precision, const DecodeArgs& a, int slots, 
     if (slots <= 0) return cudaSuccess;
     const int ch = stream_ch(precision, a.gsmax);
     if (ch && 32 * ch == a.gsmax) {
+        // the cluster form where a size above 1 is asked for (not with a lambda/partner trace)
+        if (precision != 0 && a.stream_cl > 1 && a.tr_lambda == nullptr && a.tr_partner == nullptr) {
+            const int cl = stream_cluster_size(precision, ch, a.stream_cl);
+            if (cl > 1) return launch_stream_cluster(precision, ch, cl, a, slots, st);
+        }
         if (precision >= 2) return launch_stream_half(precision, ch, a, slots, st);
         if (precision == 0) {
             if (ch == 8) return run_stream<double, 8>(a, slots, st);

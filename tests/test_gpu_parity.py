@@ -258,6 +258,52 @@ def test_streaming_tier_every_width(torch, prec, sizes):
     assert np.array_equal(res["obs"], res["obs2"]) and np.array_equal(res["flags"] & 1, res["conv"])
 
 
+def _decode_outputs(torch, g, synd, T, opts):
+    n = synd.shape[0]
+    pred = torch.empty((n,), dtype=torch.uint8, device="cuda")
+    conv = torch.empty((n,), dtype=torch.uint8, device="cuda")
+    its = torch.empty((n,), dtype=torch.int16, device="cuda")
+    g.profile_enable(True)
+    g.decode_batch(synd, T, opts, pred, conv, its)
+    torch.cuda.synchronize()
+    prof = g.profile_read()
+    g.profile_enable(False)
+    return pred.cpu().numpy(), conv.cpu().numpy(), its.cpu().numpy(), prof
+
+
+# the streaming tier's cluster form (the blocks of a thread-block cluster share one shot) gives
+# the outputs of one block per shot bit for bit, at every cluster size the width has: the
+# same rows with the same arithmetic, only distributed over several SMs
+@pytest.mark.parametrize("prec,variant", [("fp32", "bp4m"), ("fp32", "bp4mf"), ("fp32", "static"),
+                                          ("fp32", "memory"), ("fp16", "bp4m"), ("bf16", "bp4m")])
+def test_streaming_cluster_form_matches_one_block(torch, prec, variant):
+    kw = {"bp4m": dict(early_exit=True), "bp4mf": dict(decoder="bp4mf", early_exit=False),
+          "static": dict(early_exit=True, forced="static"),
+          "memory": dict(decoder="bp4mf", early_exit=False, alpha=0.7)}[variant]
+    cases = []
+    # sampled shots of the circuit graphs whose defect counts fill the 256..640-column classes
+    for d, n, T in ((17, 1500, 40), (21, 300, 30)):
+        g = pkg.Graph(d, "circuit", 0.005)
+        (synd,), _ = gpu_sample(g, 0, n, seed=d)
+        cases.append((g, synd, T))
+    # random d = 13 syndromes for the classes up to 1024 columns, several shots per cluster
+    g13 = pkg.Graph(13, "circuit", 0.005)
+    rng = np.random.default_rng(41)
+    sizes = list(rng.integers(161, 1025, size=120))
+    sb = _random_syndromes(g13.info()["n_det"][0], sizes, seed=43)
+    cases.append((g13, torch.as_tensor(pack_syndromes(sb).view(np.int32), device="cuda"), 6))
+    for g, synd, T in cases:
+        ref = _decode_outputs(torch, g, synd, T, pkg.make_opts(precision=prec, stream_cluster=1, **kw))
+        for cl in (0, 2, 4, 8, 16):
+            out = _decode_outputs(torch, g, synd, T, pkg.make_opts(precision=prec, stream_cluster=cl, **kw))
+            for a, b in zip(ref[:3], out[:3]):
+                assert np.array_equal(a, b), (g.info()["n_det"], cl)
+            # the same message updates and shots in the streaming tier
+            assert ref[3]["global"]["msg_updates"] == out[3]["global"]["msg_updates"]
+            assert ref[3]["global"]["shots"] == out[3]["global"]["shots"]
+        assert ref[3]["global"]["shots"] > 0
+
+
 def test_host_buffers_match_device_buffers(torch):
     g, og, ot = circuit_pair(5, 0.008)
     n, T = 2000, 20
