@@ -245,10 +245,13 @@ def run_serving(args, dev, serve_d):
     plain_shots = sum(o.shape[0] for _, _, o in burst) / (time.perf_counter() - t0)
     mean_req = 2048.5
     loads = []
+    # every load replays the same requests with the same arrival pattern, its gaps scaled by
+    # the load's rate, so that the loads differ only in the offered rate
+    reqs = [make_request() for _ in range(args.serve_requests)]
+    unit_gaps = rng.exponential(1.0, size=len(reqs))
     for load in [float(x) for x in str(args.serve_load).split(",") if x]:
         rate = load * cap_shots / mean_req
-        reqs = [make_request() for _ in range(args.serve_requests)]
-        gaps = rng.exponential(1.0 / rate, size=len(reqs))
+        gaps = unit_gaps / rate
         st0 = srv.stats()
         t0 = time.perf_counter()
         t_next = t0

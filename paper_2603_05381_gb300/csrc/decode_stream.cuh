@@ -10,6 +10,7 @@
 
 #include <atomic>
 #include <cstdint>
+#include <type_traits>
 
 #include "decode_smem.cuh"
 #include "device.cuh"
@@ -72,11 +73,18 @@ constexpr int kStreamWarpsOf = sizeof(T) != 4 ? kStreamWarps : CH >= 28 ? 12 : (
 template <typename T, int CH>
 constexpr int kStreamPrefetch = sizeof(T) != 4 ? 0 : CH <= 8 ? 1 : 2;
 
+// Output stage pitch in elements: a batch's W rows are read back four rows of one column per
+// thread (W/4 threads per column, 32/(W/4) columns per warp), which is free of bank
+// conflicts with an odd pitch for 32 warps and with a pitch of twice an odd number for 16
+// (and nearly so for 12).
+template <typename T, int CH, int CL = 1>
+constexpr int kStagePitch = 32 * CH + (kStreamWarpsOf<T, CH, CL> == 32 ? 1 : 2);
+
 // Dynamic shared memory of one streaming block with `stages` output stages.
 template <typename T, int CH, typename MS, int CL = 1>
 constexpr size_t stream_smem_bytes_n(int stages) {
     return (kStreamPrefetch<T, CH> != 0 ? (size_t)kStreamWarpsOf<T, CH, CL> * 3 * (32 * CH) * sizeof(T) : 0) +
-           (size_t)stages * kStreamWarpsOf<T, CH, CL> * (32 * CH + 1) * sizeof(T) + sizeof(T) +
+           (size_t)stages * kStreamWarpsOf<T, CH, CL> * kStagePitch<T, CH, CL> * sizeof(T) + sizeof(T) +
            (size_t)(32 * CH) * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 32 +
            (sizeof(MS) == 2 ? (size_t)2 * (32 * CH) * sizeof(float) : 0) + (size_t)(32 * CH) * sizeof(short);
 }
@@ -109,6 +117,26 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Four consecutive message-matrix elements from FP32 values (exact in MS): one 16-byte store
+// for FP32 storage, one 8-byte store for 16-bit storage.  p is aligned to 4 elements.
+template <typename MS, typename T>
+__device__ __forceinline__ void st4(MS* p, T a, T b, T c, T d) {
+    if constexpr (sizeof(MS) == 4) {
+        *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+    } else if constexpr (sizeof(MS) == 2) {
+        auto bits = [](T x) -> unsigned {
+            const MS v = MS(x);
+            return *reinterpret_cast<const unsigned short*>(&v);
+        };
+        *reinterpret_cast<uint2*>(p) = make_uint2(bits(a) | bits(b) << 16, bits(c) | bits(d) << 16);
+    } else {
+        p[0] = a;
+        p[1] = b;
+        p[2] = c;
+        p[3] = d;
+    }
+}
+
 // Bytes of one streaming slot: priors (T) and three message matrices (MS) of LD x LD.
 template <typename T, typename MS>
 __host__ __device__ constexpr size_t stream_slot_bytes(int ld) {
@@ -120,10 +148,11 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
     constexpr bool HALF = sizeof(MS) == 2;
     static_assert(!HALF || sizeof(T) == 4, "16-bit messages use FP32 arithmetic");
     static_assert(CL == 1 || (sizeof(T) == 4 && !TRACE && CL <= 16), "cluster form: FP32 arithmetic, no trace");
+    static_assert(W % 4 == 0, "the transposed write takes four rows per thread");
     using IO = MsgIO<MS, T>;
     constexpr int NTH = W * 32;
     constexpr int LD = 32 * CH;
-    constexpr int SP = LD + 1;  // stage pitch: odd, so the transposed read is conflict-free
+    constexpr int SP = kStagePitch<T, CH, CL>;  // output stage pitch
     // FP32 variants of up to 256 columns prefetch each warp's next row of Lg, Mc and Mo into
     // shared memory (pf[W][3][LD]) during the current row's update
     constexpr int PFM = kStreamPrefetch<T, CH>;
@@ -270,18 +299,24 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                     const T* lrow = Lg + (size_t)r * LD;
                     const MS* xrow = Mc + (size_t)r * LD;
                     const MS* orow = Mo + (size_t)r * LD;
-                    int cnt = 0, chosen = 0x7fffffff;
+                    // kept count and a kept column of the row (the only one when the count is 1,
+                    // the case in which it is used: otherwise forced convergence replaces it)
+                    int cnt = 0, kl = -1;
 #pragma unroll
                     for (int c = 0; c < CH; ++c) {
                         const int k = lane + 32 * c;
                         const T lam = lrow[k] + (down(orow + k, r) + dxg(xrow + k, k));
-                        const bool keep = lam > T(0);
-                        const unsigned bal = __ballot_sync(kFull, keep);
-                        cnt += __popc(bal);
-                        if (bal && chosen == 0x7fffffff) chosen = 32 * c + __ffs(bal) - 1;
+                        const bool kp = lam > T(0);
+                        cnt += kp ? 1 : 0;
+                        kl = kp ? k : kl;
                         if (tr_on && trl && k < s) trl[((size_t)shot * a.s_cap + r) * a.s_cap + k] = lam * (T)kLn2;
                     }
-                    if (lane == 0) bcast(&choice[r], chosen);
+#pragma unroll
+                    for (int off = 16; off; off >>= 1) {
+                        cnt += __shfl_xor_sync(kFull, cnt, off);
+                        kl = max(kl, __shfl_xor_sync(kFull, kl, off));
+                    }
+                    if (lane == 0) bcast(&choice[r], kl >= 0 ? kl : 0x7fffffff);
                     ok_all &= (cnt == 1);
                 }
                 int conv;
@@ -541,31 +576,37 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                         else if constexpr (PFM == 2) return down(pbo + lane + 32 * c, r);
                         else return down(orow + lane + 32 * c, r);
                     };
-                    if (fuse) {
-                        int cnt = 0, chosen = 0x7fffffff;
-#pragma unroll
-                        for (int c = 0; c < CH; ++c) {
-                            const T lam = LV(c) + (OV(c) + XV(c));
-                            const unsigned bal = __ballot_sync(kFull, lam > T(0));
-                            cnt += __popc(bal);
-                            if (bal && chosen == 0x7fffffff) chosen = 32 * c + __ffs(bal) - 1;
-                        }
-                        if (lane == 0) bcast(&choice[r], chosen);
-                        ok_w &= (cnt == 1);
-                    }
+                    // one pass over the row: Q = l + M[k][r]/alpha and its maximum, second
+                    // maximum and argmax; with the fused decisions also the kept count of
+                    // lambda^t = l + (M[r][k] + M[k][r]) and a kept column (the only one when
+                    // the count is 1, the case in which it is used)
                     T q[CH];
                     T m1 = ninf, m2 = ninf;
                     int am = 0x7fffffff;
+                    int cnt = 0, kl = -1;
+                    auto row_pass = [&](auto fused) {
 #pragma unroll
-                    for (int c = 0; c < CH; ++c) {
-                        const int k = lane + 32 * c;
-                        const T v = B2<T>::fma_(XV(c), ainv, LV(c));
-                        q[c] = v;
-                        const bool gt = v > m1;
-                        m2 = B2<T>::mx(m2, B2<T>::mn(v, m1));
-                        m1 = B2<T>::mx(m1, v);
-                        am = gt ? k : am;
-                    }
+                        for (int c = 0; c < CH; ++c) {
+                            const int k = lane + 32 * c;
+                            const T lv = LV(c), xv = XV(c);
+                            if constexpr (decltype(fused)::value) {
+                                const T lam = lv + (OV(c) + xv);
+                                const bool kp = lam > T(0);
+                                cnt += kp ? 1 : 0;
+                                kl = kp ? k : kl;
+                            }
+                            const T v = B2<T>::fma_(xv, ainv, lv);
+                            q[c] = v;
+                            const bool gt = v > m1;
+                            m2 = B2<T>::mx(m2, B2<T>::mn(v, m1));
+                            m1 = B2<T>::mx(m1, v);
+                            am = gt ? k : am;
+                        }
+                    };
+                    if (fuse)
+                        row_pass(std::true_type{});
+                    else
+                        row_pass(std::false_type{});
                     if constexpr (PFM == 2) {
                         // the last read of this row's buffer: the next row may replace it
                         __syncwarp();
@@ -577,6 +618,15 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                         const T o2 = __shfl_xor_sync(kFull, m2, off);
                         const int ok = __shfl_xor_sync(kFull, am, off);
                         combine_max(m1, m2, am, o1, o2, ok);
+                    }
+                    if (fuse) {
+#pragma unroll
+                        for (int off = 16; off; off >>= 1) {
+                            cnt += __shfl_xor_sync(kFull, cnt, off);
+                            kl = max(kl, __shfl_xor_sync(kFull, kl, off));
+                        }
+                        if (lane == 0) bcast(&choice[r], kl >= 0 ? kl : 0x7fffffff);
+                        ok_w &= (cnt == 1);
                     }
                     T S = T(0);
 #pragma unroll
@@ -629,9 +679,20 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                 // transposed write of the batch: Mn[k][b*W + w] = stage[w][k]
                 const int r0 = b * W;
                 const int rows = min(W, s - r0);
-                for (int e = tid; e < s * W; e += NTH) {
-                    const int k = e / W, w = e % W;
-                    if (w < rows) Mn[(size_t)k * LD + r0 + w] = MS(stage[w * SP + k]);
+                if (sizeof(T) == 4 && rows == W) {
+                    // a full batch: four consecutive rows of one column per thread, one
+                    // 16-byte (FP32) or 8-byte (16-bit) store
+                    constexpr int W4 = W / 4;
+                    for (int e = tid; e < s * W4; e += NTH) {
+                        const int k = e / W4, w = (e - k * W4) * 4;
+                        const T* sp = stage + w * SP + k;
+                        st4(Mn + (size_t)k * LD + r0 + w, sp[0], sp[SP], sp[2 * SP], sp[3 * SP]);
+                    }
+                } else {
+                    for (int e = tid; e < s * W; e += NTH) {
+                        const int k = e / W, w = e % W;
+                        if (w < rows) Mn[(size_t)k * LD + r0 + w] = MS(stage[w * SP + k]);
+                    }
                 }
                 // one stage: the next batch may overwrite it only after this write; two stages:
                 // the next batch writes the other one, and the barrier after its rows (which

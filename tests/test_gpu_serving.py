@@ -116,6 +116,28 @@ def test_budget_evicts_and_refuses(graphs):
     srv.close()
 
 
+def test_heavy_scratch_is_outside_the_budget(graphs):
+    # the budget covers per-shot buffers only; the streaming tier's scratch of a heavy graph
+    # (hundreds of MB here) is outside it, so a budget that holds the per-shot buffers of the
+    # d = 25 and d = 5 workspaces serves both graphs without evicting or refusing either
+    g25, g5 = graphs[3], graphs[0]
+    s25 = _host_syndromes(g25, 300, seed=51)
+    s5 = _host_syndromes(g5, 300, seed=52)
+    opts = pkg.make_opts(precision="fp32")
+    cap = 1024
+    w = sum(cap * (s.shape[1] * 4 + 5 + 9 * 4) for s in (s25, s5))
+    srv = pkg.Server(slots=1, max_batch_shots=cap, device_budget_bytes=int(1.1 * w))
+    a, b = srv.add_graph(g25), srv.add_graph(g5)
+    for rep in range(2):
+        for gid, g, synd in ((a, g25, s25), (b, g5, s5)):
+            pred = np.empty(synd.shape[0], dtype=np.uint8)
+            srv.wait(srv.submit(gid, synd, T, opts, pred))
+            assert np.array_equal(pred, _alone(g, synd, opts)[0])
+    st = srv.stats()
+    srv.close()
+    assert st["evictions"] == 0
+
+
 def test_rejects_device_buffers_and_bbp4mf(graphs):
     torch = torch_cuda()
     g = graphs[0]
