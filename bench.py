@@ -368,7 +368,8 @@ def run_fused(args, dev):
         agree = sum(int((o == p).sum()) for o, p in zip(outs, plain)) / total
         out[prec] = {"shots_per_s": total / dt, "vs_plain_fp32": total / dt / out["plain_fp32_shots_per_s"],
                      "outputs_equal_to_fp32_plain": agree, "tier_plan": info["plan"],
-                     "plan_ms": info["plan_ms"]}
+                     "plan_ms": info["plan_ms"], "stream_cluster": info["stream_cluster"],
+                     "stream_ms": info["stream_ms"]}
     for g in graphs:
         g.close()
     return out

@@ -388,6 +388,10 @@ typedef struct {
     int64_t runs;         /* completed runs */
     int64_t graph_replays;/* runs replayed from the captured CUDA graph */
     uint64_t msg_updates; /* message updates of the last run */
+    int stream_cluster;   /* streaming tier's cluster size the autotuner kept (1: one block per
+                             shot), or the one opts asked for */
+    double stream_ms[2];  /* autotuner timings of the chosen plan with one block per shot and
+                             with the cluster form (ms; 0 where not timed) */
 } bp4m_multi_info_t;
 
 bp4m_multi* bp4m_multi_create(int n, bp4m_graph* const* graphs, const int* types, const int64_t* max_shots,

@@ -275,7 +275,7 @@ class Multi:
         mi = _capi.MultiInfo()
         check(load().bp4m_multi_info(self._h, ctypes.byref(mi)))
         return {"plan": mi.plan, "plan_ms": list(mi.plan_ms), "runs": mi.runs, "graph_replays": mi.graph_replays,
-                "msg_updates": mi.msg_updates}
+                "msg_updates": mi.msg_updates, "stream_cluster": mi.stream_cluster, "stream_ms": list(mi.stream_ms)}
 
     def close(self):
         if getattr(self, "_h", None):

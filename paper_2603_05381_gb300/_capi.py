@@ -90,7 +90,8 @@ class ServerStats(ctypes.Structure):
 
 class MultiInfo(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_int), ("plan_ms", ctypes.c_double * 3), ("runs", ctypes.c_int64),
-                ("graph_replays", ctypes.c_int64), ("msg_updates", ctypes.c_uint64)]
+                ("graph_replays", ctypes.c_int64), ("msg_updates", ctypes.c_uint64),
+                ("stream_cluster", ctypes.c_int), ("stream_ms", ctypes.c_double * 2)]
 
 
 _P = ctypes.c_void_p

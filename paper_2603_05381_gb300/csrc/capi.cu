@@ -1200,6 +1200,8 @@ struct bp4m_multi {
     int plan = 0;
     bool tuned = false;
     double plan_ms[kPlanCount] = {0, 0, 0};
+    int stream_cl = 1;                 // streaming tier's cluster size (autotuner or opts)
+    double stream_ms[2] = {0, 0};      // chosen plan with one block per shot / cluster form
     bool use_graph = true;
     cudaGraphExec_t exec = nullptr;
     std::vector<int64_t> graph_shots;  // shot vector the captured graph was made for
@@ -1231,7 +1233,7 @@ void multi_free(bp4m_multi* m) {
 }
 
 // Everything of one run after the host staging is filled; no host synchronisation.
-int multi_enqueue(bp4m_multi* m, const std::vector<int64_t>& shots, int plan) {
+int multi_enqueue(bp4m_multi* m, const std::vector<int64_t>& shots, int plan, int stream_cl) {
     cudaStream_t st = m->st;
     const int n = (int)m->e.size();
     for (int k = 0; k < n; ++k) {
@@ -1256,7 +1258,7 @@ int multi_enqueue(bp4m_multi* m, const std::vector<int64_t>& shots, int plan) {
     a.early_exit = m->opts.early_exit ? 1 : 0;
     a.decoder = m->opts.decoder;
     a.forced_static = m->opts.forced == BP4M_FORCED_STATIC ? 1 : 0;
-    a.stream_cl = m->opts.stream_cluster;
+    a.stream_cl = stream_cl;
     a.alpha = m->opts.alpha;
     a.ctr = m->ctr;
     for (int tier = 1; tier < kGlobalTier; ++tier) {
@@ -1559,21 +1561,38 @@ int bp4m_multi_run(bp4m_multi* m, const uint32_t* const* syndromes, const int64_
         cudaEvent_t e0, e1;
         CK(cudaEventCreate(&e0));
         CK(cudaEventCreate(&e1));
-        for (int pl = 0; pl < kPlanCount; ++pl) {
-            int rc = multi_enqueue(m, sh, pl);  // warm (first use of the plan's kernels)
+        // time one plan: a warm run (first use of its kernels), then a timed one
+        auto time_plan = [&](int pl, int cl, double* ms_out) -> int {
+            int rc = multi_enqueue(m, sh, pl, cl);
             if (rc) return rc;
             CK(cudaEventRecord(e0, m->st));
-            rc = multi_enqueue(m, sh, pl);
+            rc = multi_enqueue(m, sh, pl, cl);
             if (rc) return rc;
             CK(cudaEventRecord(e1, m->st));
             CK(cudaEventSynchronize(e1));
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, e0, e1));
-            m->plan_ms[pl] = ms;
+            *ms_out = ms;
+            return BP4M_OK;
+        };
+        const int cl_opt = m->opts.stream_cluster;
+        const int cl0 = cl_opt > 1 ? cl_opt : 1;
+        for (int pl = 0; pl < kPlanCount; ++pl) {
+            const int rc = time_plan(pl, cl0, &m->plan_ms[pl]);
+            if (rc) return rc;
+        }
+        m->plan = (int)(std::min_element(m->plan_ms, m->plan_ms + kPlanCount) - m->plan_ms);
+        m->stream_cl = cl0;
+        // the streaming tier's block shape: with the automatic choice, the chosen plan once
+        // more with the cluster form (each width's default size), kept if faster
+        if (cl_opt == 0 && m->pio != 0 && m->max_defects > tier_plan(m->pio).smax[kGlobalTier - 1]) {
+            m->stream_ms[0] = m->plan_ms[m->plan];
+            const int rc = time_plan(m->plan, 16, &m->stream_ms[1]);
+            if (rc) return rc;
+            if (m->stream_ms[1] < m->stream_ms[0]) m->stream_cl = 16;
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        m->plan = (int)(std::min_element(m->plan_ms, m->plan_ms + kPlanCount) - m->plan_ms);
         m->tuned = true;
     } else if (m->use_graph) {
         if (!m->exec || m->graph_shots != sh) {
@@ -1581,7 +1600,7 @@ int bp4m_multi_run(bp4m_multi* m, const uint32_t* const* syndromes, const int64_
             m->exec = nullptr;
             cudaGraph_t graph;
             CK(cudaStreamBeginCapture(m->st, cudaStreamCaptureModeThreadLocal));
-            const int rc = multi_enqueue(m, sh, m->plan);
+            const int rc = multi_enqueue(m, sh, m->plan, m->stream_cl);
             const cudaError_t ce = cudaStreamEndCapture(m->st, &graph);
             if (rc) return rc;
             CK(ce);
@@ -1593,7 +1612,7 @@ int bp4m_multi_run(bp4m_multi* m, const uint32_t* const* syndromes, const int64_
         CK(cudaGraphLaunch(m->exec, m->st));
         ++m->replays;
     } else {
-        const int rc = multi_enqueue(m, sh, m->plan);
+        const int rc = multi_enqueue(m, sh, m->plan, m->stream_cl);
         if (rc) return rc;
     }
     CK(cudaStreamSynchronize(m->st));
@@ -1617,6 +1636,9 @@ int bp4m_multi_info(const bp4m_multi* m, bp4m_multi_info_t* out) {
     out->runs = m->runs;
     out->graph_replays = m->replays;
     out->msg_updates = m->h_ctr ? m->h_ctr[C_MSGS] : 0;
+    out->stream_cluster = m->stream_cl;
+    out->stream_ms[0] = m->stream_ms[0];
+    out->stream_ms[1] = m->stream_ms[1];
     return BP4M_OK;
 }
 

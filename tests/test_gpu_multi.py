@@ -59,6 +59,9 @@ def test_fused_runs_match_decode_alone(setup, prec):
     print("%s fused: plan %d (%s ms), runs %d, replays %d" % (prec, info["plan"], [round(x, 2) for x in info["plan_ms"]],
                                                               info["runs"], info["graph_replays"]))
     assert info["runs"] == 3 and info["graph_replays"] == 2 and min(info["plan_ms"]) > 0
+    # the autotuner also timed the streaming tier's cluster form (max_defects is above the
+    # shared-memory tiers) and kept the faster block shape
+    assert min(info["stream_ms"]) > 0 and info["stream_cluster"] in (1, 16)
     # a new shot vector: the graph is captured again
     half = [c // 2 for c in caps]
     outs = [np.empty(h, dtype=np.uint8) for h in half]
@@ -66,6 +69,25 @@ def test_fused_runs_match_decode_alone(setup, prec):
     for (p0, _), o, h in zip(want, outs, half):
         assert np.array_equal(o, p0[:h])
     assert m.info()["graph_replays"] == 3
+    m.close()
+
+
+def test_fused_cluster_form_as_asked(setup):
+    # a requested streaming cluster size is used as is (no timing of the alternative); outputs
+    # equal decode alone
+    entries = setup
+    graphs = [g for g, _, _ in entries]
+    types = [ty for _, ty, _ in entries]
+    caps = [s.shape[0] for _, _, s in entries]
+    want = [_alone(g, ty, s, "fp32") for g, ty, s in entries]
+    m = pkg.Multi(graphs, caps, T, pkg.make_opts(precision="fp32", stream_cluster=4), types=types, max_defects=256)
+    for rep in range(2):
+        outs = [np.full(c, 9, dtype=np.uint8) for c in caps]
+        m.run([s for _, _, s in entries], outs)
+        for (p0, _), o in zip(want, outs):
+            assert np.array_equal(o, p0)
+    info = m.info()
+    assert info["stream_cluster"] == 4 and info["stream_ms"] == [0.0, 0.0]
     m.close()
 
 
