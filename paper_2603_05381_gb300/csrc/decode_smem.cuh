@@ -1031,19 +1031,8 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                         const int ok = __shfl_xor_sync(kFull, am, off);
                         combine_max(m1, m2, am, o1, o2, ok);
                     }
-                T S;
-                if constexpr (std::is_same<T, float>::value) {
-                    const float2 nm2 = make_float2(-m2, -m2);
-                    float2 s2 = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int j = 0; j < CH / 2; ++j) {
-                        const float2 dq = __fadd2_rn(make_float2(fminf(q.p[j].x, m2), fminf(q.p[j].y, m2)), nm2);
-                        const float2 u = make_float2(B2<float>::ex2(dq.x), B2<float>::ex2(dq.y));
-                        q.p[j] = u;
-                        s2 = __fadd2_rn(s2, u);
-                    }
-                    S = s2.x + s2.y;
-                } else {
+                    // FP64 (16-bit storage runs only with FP32 arithmetic)
+                    static_assert(!HALF, "16-bit storage is FP32 only");
                     T sa = T(0), sb = T(0);
 #pragma unroll
                     for (int c = 0; c < CH; c += 2) {
@@ -1056,83 +1045,29 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
                             sb += w;
                         }
                     }
-                    S = sa + sb;
-                }
+                    T S = sa + sb;
 #pragma unroll
-                for (int off = R; off < 32; off <<= 1) S += __shfl_xor_sync(kFull, S, off);
-                const T cf = B2<T>::ex2(m2 - m1);
-                const T Aa = B2<T>::fma_(cf, S - T(1), T(1));
-                // 16-bit storage: this row's reference r_i = m1 rounded to the format (so that
-                // it is exact there), stored values out + r_i = -lg2(Aa - cf u) + (r_i - m1)
-                T rf = T(0), dref = T(0);
-                if constexpr (HALF) {
-                    rf = IO::unpack(IO::pack(m1, 0.f)).x;
-                    dref = rf - m1;
-                }
-                if (act) {
-                    if constexpr (std::is_same<T, float>::value) {
-                        // out = -m1 - lg2(Aa - cf u), the subtraction as an exact fma with -1
-                        const float2 ncf = make_float2(-cf, -cf), A2 = make_float2(Aa, Aa);
-                        const float2 nm1 = HALF ? make_float2(dref, dref) : make_float2(-m1, -m1);
-                        const float2 neg1 = make_float2(-1.f, -1.f);
-#pragma unroll
-                        for (int j = 0; j < CH / 2; ++j) {
-                            const float2 y = __ffma2_rn(ncf, q.p[j], A2);
-                            const float2 lg = make_float2(B2<float>::lg2(y.x), B2<float>::lg2(y.y));
-                            const float2 out = __ffma2_rn(lg, neg1, nm1);
-                            if constexpr (HALF) {
-                                // store the rounded pair (relative to r_i); the register copy is
-                                // the stored value decoded as every reader decodes it, so that
-                                // both ends of a variable see the same message
-                                const unsigned pk2 = IO::pack(out.x, out.y);
-                                *reinterpret_cast<unsigned short*>(CMP(2 * j)) = (unsigned short)(pk2 & 0xFFFFu);
-                                *reinterpret_cast<unsigned short*>(CMP(2 * j + 1)) = (unsigned short)(pk2 >> 16);
-                                if constexpr (REG) mo.p[j] = __fadd2_rn(IO::unpack(pk2), make_float2(-rf, -rf));
-                            } else {
-                                *CMP(2 * j) = out.x;
-                                *CMP(2 * j + 1) = out.y;
-                                if constexpr (REG) mo.p[j] = out;
-                            }
-                        }
-                    } else {
+                    for (int off = R; off < 32; off <<= 1) S += __shfl_xor_sync(kFull, S, off);
+                    const T cf = B2<T>::ex2(m2 - m1);
+                    const T Aa = B2<T>::fma_(cf, S - T(1), T(1));
+                    if (act) {
 #pragma unroll
                         for (int c = 0; c < CH; ++c) {
                             const T out = -m1 - B2<T>::lg2(B2<T>::fma_(-cf, q[c], Aa));
                             *CMP(c) = out;
                             if (REG) mo[REG ? c : 0] = out;
                         }
-                    }
-                    T oam = -m2 - B2<T>::lg2(S - T(1));
-                    if constexpr (HALF) {
-                        const float st_am = __fmaf_rn(B2<float>::lg2(S - 1.f), -1.f, rf - m2);
-                        if (owner_of<PAIR, G>(am) == g) IO::st(Mt + am * PM + i, st_am);
-                        oam = IO::unpack(IO::pack(st_am, 0.f)).x + (-rf);
-                    } else if (owner_of<PAIR, G>(am) == g) {
-                        IO::st(Mt + am * PM + i, oam);
-                    }
-                    if (REG) {
-                        am_prev = am;
-                        out_am = oam;
-                        if constexpr (std::is_same<T, float>::value) {
-                            // what the packed output loop wrote for the argmax column: u = ex2(0)
-                            const float u0 = B2<float>::ex2(0.f);
-                            float og = __fmaf_rn(B2<float>::lg2(__fmaf_rn(-cf, u0, Aa)), -1.f, HALF ? dref : -m1);
-                            if constexpr (HALF) og = IO::unpack(IO::pack(og, 0.f)).x + (-rf);
-                            out_am_gen = og;
+                        const T oam = -m2 - B2<T>::lg2(S - T(1));
+                        if (owner_of<PAIR, G>(am) == g) IO::st(Mt + am * PM + i, oam);
+                        if (REG) {
+                            am_prev = am;
+                            out_am = oam;
                         }
-                    }
-                    if (own_diag) {
-                        if constexpr (HALF) {
-                            // the diagonal holds r_i, which decodes to exactly 0
-                            if (!REG) Dg[i] = IO::ld(Mt + i * PM + i) + (-rf);
-                            IO::st(Mt + i * PM + i, rf);
-                            nrefv[i] = -rf;
-                        } else {
+                        if (own_diag) {
                             if (!REG) Dg[i] = IO::ld(Mt + i * PM + i);
                             Mt[i * PM + i] = MS(0.f);
                         }
                     }
-                }
                 }
             }
             __syncthreads();
