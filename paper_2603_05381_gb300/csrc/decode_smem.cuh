@@ -347,7 +347,13 @@ __global__ void __launch_bounds__(CH * G * G, blocks_for(CH * G * G, (int)sizeof
     const bool full = (a.decoder == 1) || !a.early_exit;
     T* trl = reinterpret_cast<T*>(a.tr_lambda);
     const T ninf = Num<T>::ninf();
-    unsigned long long acc_it = 0, acc_msg = 0, acc_def = 0, acc_shots = 0, acc_fc = 0, acc_fcr = 0;
+    // counters of this block's shots: updated by thread 0 only, so kept in shared memory rather
+    // than in twelve registers of every thread
+    __shared__ unsigned long long sh_acc[6];
+    unsigned long long &acc_it = sh_acc[0], &acc_msg = sh_acc[1], &acc_def = sh_acc[2], &acc_shots = sh_acc[3],
+                       &acc_fc = sh_acc[4], &acc_fcr = sh_acc[5];
+    if (tid == 0)
+        for (int k = 0; k < 6; ++k) sh_acc[k] = 0;
 
     T* const row_l = Lm + i * P + k0;    // priors l_ik, register c at [col_off(c)]
     MS* const row_m = Mt + i * PM + k0;  // incoming messages M[k][i]
