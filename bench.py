@@ -39,8 +39,8 @@ KERNEL_OF = {"tier1": "decode_smem_kernel<float, CH=32, G=1> (s <= 32)",
 # DRAM bytes (read + write) per decoded shot of each FP32 tier kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the 65,536-shot case of this workload,
 # divided by the shots the launch decoded; a full launch's traffic is this times its shots.
-DRAM_BYTES_PER_SHOT = {"tier4": 8.546e6 / 10172, "tier5": 12.016e6 / 26656, "tier6": 11.049e6 / 21645,
-                       "tier7": 7.465e6 / 5503}
+DRAM_BYTES_PER_SHOT = {"tier4": 8.536e6 / 10172, "tier5": 12.013e6 / 26656, "tier6": 11.048e6 / 21645,
+                       "tier7": 7.452e6 / 5503}
 METRIC = "decoded shots/s & msg-updates/s vs HBM roofline (d=13 circuit); p50/p99 latency"
 WORKLOAD = "rotated surface code memory-Z circuit, d=13, 13 rounds, uniform depolarizing p=0.005 " \
            "(gates, idles, data before rounds, reset/measure flips); 10^6 shots per step; BP4M, " \
