@@ -36,11 +36,18 @@ KERNEL_OF = {"tier1": "decode_smem_kernel<float, CH=32, G=1> (s <= 32)",
              "tier6": "decode_smem_kernel<float, CH=36, G=4> (s <= 144)",
              "tier7": "decode_smem_kernel<float, CH=40, G=4> (s <= 160)",
              "global": "decode_stream_kernel<float> (s > 160)"}
+# the 113..144-defect tiers in the register-tile form (--tile-form 2, or 0 when it is the
+# library's default)
+REG_TILES_DEFAULT = False
+KERNEL_OF_REG = {"tier5": "decode_reg_kernel<NB=32, B=4> (s <= 128)",
+                 "tier6": "decode_reg_kernel<NB=24, B=6> (s <= 144)"}
 # DRAM bytes (read + write) per decoded shot of each FP32 tier kernel, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum) of the 65,536-shot case of this workload,
 # divided by the shots the launch decoded; a full launch's traffic is this times its shots.
 DRAM_BYTES_PER_SHOT = {"tier4": 8.536e6 / 10172, "tier5": 12.013e6 / 26656, "tier6": 11.048e6 / 21645,
                        "tier7": 7.452e6 / 5503}
+# the same with the register-tile form of tiers 5 and 6 (not yet captured for those two)
+DRAM_BYTES_PER_SHOT_REG = {"tier4": DRAM_BYTES_PER_SHOT["tier4"], "tier7": DRAM_BYTES_PER_SHOT["tier7"]}
 METRIC = "decoded shots/s & msg-updates/s vs HBM roofline (d=13 circuit); p50/p99 latency"
 WORKLOAD = "rotated surface code memory-Z circuit, d=13, 13 rounds, uniform depolarizing p=0.005 " \
            "(gates, idles, data before rounds, reset/measure flips); 10^6 shots per step; BP4M, " \
@@ -61,6 +68,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     # message storage: fp32 (the configuration's, default) or the 16-bit forms (FP32 math)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    # FP32 tiers of 113..144 defects: 0 = the library's default, 1 = row form, 2 = register tiles
+    ap.add_argument("--tile-form", type=int, default=0, choices=[0, 1, 2])
     # decoding-service measurement: circuit graphs of these distances (p = 0.005; the
     # default is every odd distance 5..25), requests of 1..4096 shots arriving as a Poisson
     # process at a fraction of the measured capacity
@@ -388,7 +397,7 @@ def run_ours(args, rank, world, local):
     mufu = pkg.probe_mufu()
     g = pkg.Graph(D, "circuit", P)
     info = g.info()
-    opts = pkg.make_opts(precision=args.precision, early_exit=True, decoder="bp4m")
+    opts = pkg.make_opts(precision=args.precision, early_exit=True, decoder="bp4m", tile_form=args.tile_form)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     shots = args.shots
@@ -447,6 +456,11 @@ def run_ours(args, rank, world, local):
     value = all_shots / (t_max / 1e3)
 
     # ---- roofline of the dominant kernel (largest share of event-timed decode time)
+    kernel_of = dict(KERNEL_OF)
+    reg_form = args.precision == "fp32" and (args.tile_form == 2 or (args.tile_form == 0 and REG_TILES_DEFAULT))
+    if reg_form:
+        kernel_of.update(KERNEL_OF_REG)
+    traffic_of = DRAM_BYTES_PER_SHOT_REG if reg_form else DRAM_BYTES_PER_SHOT
     slots = ["tier%d" % k for k in range(1, 8)] + ["global"]
     dom = max(slots, key=lambda s: prof[s]["ms"])
     dp = prof[dom]
@@ -491,6 +505,7 @@ def run_ours(args, rank, world, local):
         "config": {"workload": WORKLOAD.replace("FP32 messages", {"fp32": "FP32 messages", "fp16": "FP16 messages (FP32 arithmetic)", "bf16": "BF16 messages (FP32 arithmetic)"}[args.precision]), "d": D, "p": P, "rounds": D, "detectors": info["n_det"][0],
                    "graph_edges": info["n_edges"][0], "shots_per_step": shots, "iters": T,
                    "decoder": "BP4M early exit", "precision": args.precision,
+                   "tiles_113_144": "register tiles" if reg_form else "rows",
                    "l2": "256 MB buffer written between timed steps; per-step syndromes (148 MB) exceed L2",
                    "parallelism": "shots sharded across ranks, no collective on the data path"},
         "msg_updates_per_s": all_msg / (t_max / 1e3),
@@ -499,10 +514,10 @@ def run_ours(args, rank, world, local):
         "unconverged_fraction": totals["unconv"] / max(totals["shots"], 1),
         "ler": totals["fail"] / max(totals["shots"], 1),
         "mean_iters": totals["iters"] / max(totals["shots"], 1),
-        "roofline": {"bound": "alu", "kernel": KERNEL_OF.get(dom, dom), "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": kernel_of.get(dom, dom), "achieved": achieved,
                      "peak": peak, "unit": "Gmsg/s", "frac": achieved / peak,
-                     "traffic": (DRAM_BYTES_PER_SHOT[dom] * dp["shots"] / max(dp["launches"], 1)
-                                 if dom in DRAM_BYTES_PER_SHOT and args.precision == "fp32" else None),
+                     "traffic": (traffic_of[dom] * dp["shots"] / max(dp["launches"], 1)
+                                 if dom in traffic_of and args.precision == "fp32" else None),
                      "traffic_unit": "bytes per launch (ncu DRAM read + write, 65,536-shot capture scaled by shots)",
                      "peak_basis": "MUFU, measured in this run by bp4m_probe_mufu: one ex2 (%.2f/clk/SM) + one "
                                    "lg2 (%.2f/clk/SM) per message update = %.4f SM-cycles; x %d SMs x %.0f MHz "

@@ -60,16 +60,18 @@ def _stream(stream):
 
 
 def make_opts(precision=FP32, early_exit=True, decoder="bp4m", alpha=1.0, type=0, forced="greedy",
-              stream_cluster=0):
+              stream_cluster=0, tile_form=0):
     """Decoder options (bp4m_opts).  forced: "greedy" (global greedy forced convergence) or
     "static" (the paper's static partition of the variables into per-factor blocks).
     stream_cluster: thread blocks sharing one shot in the streaming tier (0 = by width,
-    1 = one block per shot, 2/4/8/16 = that size where available); outputs do not depend on it."""
+    1 = one block per shot, 2/4/8/16 = that size where available); outputs do not depend on it.
+    tile_form: FP32 tiers of 113..144 defects, 0 = library default, 1 = row form, 2 = register tiles."""
     dec = ({"bp4m": DEC_BP4M, "bp4mf": DEC_BP4MF, "bbp4mf": DEC_BBP4MF}[decoder] if isinstance(decoder, str)
            else int(decoder))
     prec = {"fp32": FP32, "fp64": FP64, "fp16": FP16, "bf16": BF16}[precision] if isinstance(precision, str) else int(precision)
     fc = {"greedy": 0, "static": 1}[forced] if isinstance(forced, str) else int(forced)
-    return _capi.Opts(prec, 1 if early_exit else 0, dec, float(alpha), int(type), fc, int(stream_cluster))
+    return _capi.Opts(prec, 1 if early_exit else 0, dec, float(alpha), int(type), fc, int(stream_cluster),
+                      int(tile_form))
 
 
 class Graph:

@@ -39,7 +39,7 @@ class Noise(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("early_exit", ctypes.c_int), ("decoder", ctypes.c_int),
                 ("alpha", ctypes.c_double), ("type", ctypes.c_int), ("forced", ctypes.c_int),
-                ("stream_cluster", ctypes.c_int)]
+                ("stream_cluster", ctypes.c_int), ("tile_form", ctypes.c_int)]
 
 
 class Counts(ctypes.Structure):

@@ -14,9 +14,9 @@ LIB = os.path.join(HERE, "libbp4m.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CUDA_SRCS = ["capi.cu", "kernels_decode.cu", "kernels_half.cu", "kernels_cluster.cu", "kernels_cluster_half.cu",
-             "kernels_rw.cu", "kernels_misc.cu", "kernels_bbp.cu"]
+             "kernels_rw.cu", "kernels_misc.cu", "kernels_bbp.cu", "kernels_reg.cu"]
 CXX_SRCS = ["host_graph.cpp"]
-HEADERS = ["device.cuh", "decode_smem.cuh", "decode_stream.cuh", "host_graph.h"]
+HEADERS = ["device.cuh", "decode_smem.cuh", "decode_stream.cuh", "decode_reg.cuh", "host_graph.h"]
 
 
 def _nvcc():

@@ -503,6 +503,7 @@ int check_opts(const bp4m_graph* g, const bp4m_opts* o, int iters) {
     if (o->stream_cluster != 0 && o->stream_cluster != 1 && o->stream_cluster != 2 && o->stream_cluster != 4 &&
         o->stream_cluster != 8 && o->stream_cluster != 16)
         return fail(BP4M_EINVAL, "stream_cluster must be 0, 1, 2, 4, 8 or 16");
+    if (o->tile_form < 0 || o->tile_form > 2) return fail(BP4M_EINVAL, "tile_form must be 0, 1 or 2");
     return BP4M_OK;
 }
 
@@ -548,6 +549,7 @@ int decode_device(bp4m_graph* g, Workspace& w, int ty, const uint32_t* synd, int
     a.decoder = o->decoder;
     a.forced_static = o->forced == BP4M_FORCED_STATIC ? 1 : 0;
     a.stream_cl = o->stream_cluster;
+    a.tile_form = o->tile_form;
     a.alpha = o->alpha;
     a.obs_pred = obs_pred;
     a.flags = flags;
@@ -939,7 +941,7 @@ bool same_batch(const SrvRequest& a, const SrvRequest& b) {
     return a.graph == b.graph && a.iters == b.iters && a.opts.precision == b.opts.precision &&
            a.opts.early_exit == b.opts.early_exit && a.opts.decoder == b.opts.decoder &&
            a.opts.alpha == b.opts.alpha && a.opts.type == b.opts.type && a.opts.forced == b.opts.forced &&
-           a.opts.stream_cluster == b.opts.stream_cluster;
+           a.opts.stream_cluster == b.opts.stream_cluster && a.opts.tile_form == b.opts.tile_form;
 }
 
 }  // namespace
@@ -1258,6 +1260,7 @@ int multi_enqueue(bp4m_multi* m, const std::vector<int64_t>& shots, int plan, in
     a.early_exit = m->opts.early_exit ? 1 : 0;
     a.decoder = m->opts.decoder;
     a.forced_static = m->opts.forced == BP4M_FORCED_STATIC ? 1 : 0;
+    a.tile_form = m->opts.tile_form;
     a.stream_cl = stream_cl;
     a.alpha = m->opts.alpha;
     a.ctr = m->ctr;
@@ -2013,6 +2016,7 @@ int bp4m_decode_noalloc(const bp4m_graph* g, const uint32_t* syndromes, int64_t 
     a.decoder = opts->decoder;
     a.forced_static = opts->forced == BP4M_FORCED_STATIC ? 1 : 0;
     a.stream_cl = opts->stream_cluster;
+    a.tile_form = opts->tile_form;
     a.alpha = opts->alpha;
     a.obs_pred = obs_pred;
     a.flags = converged;

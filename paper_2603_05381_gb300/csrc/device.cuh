@@ -114,6 +114,7 @@ struct DecodeArgs {
     int64_t gslot_elems = 0;         // elements per slot for each of the three matrices
     int gsmax = 0;                   // largest s a slot holds
     int stream_cl = 0;               // streaming tier's cluster size (stream_cluster_for); 0 or 1: none
+    int tile_form = 0;               // FP32 shared-memory tiers: 0 = library default, 1 = rows, 2 = register tiles
 };
 
 #ifdef __CUDACC__
@@ -212,6 +213,10 @@ cudaError_t launch_classify(const uint32_t* synd, int64_t shots, int n_words,
                             const uint8_t* skip_obs, const int16_t* skip_iters, cudaStream_t st,
                             int64_t list_stride = 0 /* 0: shots */, int32_t item_base = 0);
 
+// Register-tile form of the FP32 shared-memory tiers (decode_reg.cuh): tiers that have one,
+// and its launch (or, with prepare_only, its one-time kernel attributes).
+bool reg_tier_available(int tier);
+cudaError_t launch_decode_tier_reg(int tier, const DecodeArgs& a, int num_sms, cudaStream_t st, bool prepare_only);
 // 16-bit message storage (precision 2 = IEEE half, 3 = bfloat16) of the shared-memory tiers.
 cudaError_t launch_decode_tier_half(int precision, int tier, const DecodeArgs& a, int num_sms, cudaStream_t st,
                                     bool prepare_only);

@@ -381,8 +381,20 @@ std::atomic<void*> g_noalloc_addr[kMaxDevices];
 template <typename T>
 cudaError_t dispatch_tier(int tier, const DecodeArgs& a, int num_sms, cudaStream_t st, bool prep);
 
+// Form of the FP32 tiers that have both when the caller leaves the choice to the library
+constexpr bool kRegTilesDefault = false;
+
 template <>
 cudaError_t dispatch_tier<float>(int tier, const DecodeArgs& a, int num_sms, cudaStream_t st, bool prep) {
+    // the register-tile form where the tier has one (both forms are prepared)
+    if (reg_tier_available(tier)) {
+        if (prep) {
+            cudaError_t e = launch_decode_tier_reg(tier, a, num_sms, st, true);
+            if (e != cudaSuccess) return e;
+        } else if (a.tile_form == 2 || (a.tile_form == 0 && kRegTilesDefault)) {
+            return launch_decode_tier_reg(tier, a, num_sms, st, false);
+        }
+    }
     switch (tier) {
         case 1: return run_tier2<float, 32, 1, kReg32[1]>(a, num_sms, st, prep);
         case 2: return run_tier2<float, 32, 2, kReg32[2]>(a, num_sms, st, prep);

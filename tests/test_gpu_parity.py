@@ -220,6 +220,51 @@ def test_every_tier_boundary_d13(torch, prec, early):
     assert np.array_equal(res["obs"], res["obs2"]) and np.array_equal(res["flags"] & 1, res["conv"])
 
 
+# The 113..144-defect tiers in both forms: register tiles (a thread holds a block of the message
+# matrix and its mirror) and rows (messages in shared memory).  Posteriors after exactly
+# T iterations against the oracle's, and every decoder variant's decisions against the oracle
+# (margin rule); both forms must meet the same bars.
+_REG_SIZES = [113, 118, 125, 127, 128, 129, 134, 141, 143, 144]
+
+
+@pytest.mark.parametrize("form", [2, 1])
+def test_register_tiles_posteriors(torch, form):
+    g, og, ot = circuit_pair(13, 0.005)
+    sb = _random_syndromes(og.n_det, _REG_SIZES, seed=71)
+    synd = torch.as_tensor(pack_syndromes(sb).view(np.int32), device="cuda")
+    worst = 0.0
+    for T in (1, 3, 8):
+        res = gpu_decode(g, synd, T, pkg.make_opts(precision="fp32", early_exit=False, tile_form=form), s_cap=144)
+        assert list(res["s"]) == _REG_SIZES
+        for k, s in enumerate(_REG_SIZES):
+            dets = np.flatnonzero(sb[k])
+            L = ot.L[np.ix_(dets, dets)]
+            lam = run_bp(L, T)[-1][1]
+            got = res["lam"][k][:s, :s].astype(np.float64)
+            worst = max(worst, float(np.max(np.abs(got - lam) / (np.abs(L) + 1.0))))
+    print("form %d: worst |dlambda|/(|l|+1) = %.3g" % (form, worst))
+    assert worst < 1e-4
+
+
+@pytest.mark.parametrize("form", [2, 1])
+@pytest.mark.parametrize("decoder,early,alpha,forced", [("bp4m", True, 1.0, "greedy"), ("bp4m", False, 1.0, "greedy"),
+                                                        ("bp4mf", True, 1.0, "greedy"), ("bp4mf", True, 0.85, "greedy"),
+                                                        ("bp4m", True, 1.0, "static")])
+def test_register_tiles_decisions(torch, form, decoder, early, alpha, forced):
+    g, og, ot = circuit_pair(13, 0.005)
+    sb = _random_syndromes(og.n_det, _REG_SIZES, seed=72)
+    synd = torch.as_tensor(pack_syndromes(sb).view(np.int32), device="cuda")
+    T = 10
+    opts = pkg.make_opts(precision="fp32", early_exit=early, decoder=decoder, alpha=alpha, forced=forced,
+                         tile_form=form)
+    res = gpu_decode(g, synd, T, opts, s_cap=144)
+    cnt, bad = compare_shots(ot, sb, res, T, range(len(_REG_SIZES)), TAU32, decoder=decoder, early_exit=early,
+                             alpha=alpha, forced=forced)
+    print("form %d %s: %d/%d differ %s" % (form, decoder, len(bad), cnt, bad))
+    assert all(m < TAU32 for _, m in bad), bad
+    assert np.array_equal(res["obs"], res["obs2"]) and np.array_equal(res["flags"] & 1, res["conv"])
+
+
 # the streaming tier's column count follows the batch's largest defect count: 192, 256, 320,
 # 384, 448, 512, 640, 768, 896 or 1024 columns in FP32 (256 or 512 in FP64); every width
 # once, with the posteriors after exactly T iterations and the early-exit decisions against
