@@ -102,12 +102,13 @@ typedef struct {
                         such clusters, else the width's default.  The outputs do not depend
                         on it. */
     int tile_form;   /* FP32 shared-memory tiers of 113..144 unsatisfied detectors: 0 (default)
-                        = the library's choice (register tiles); 1 = the row form (messages in
-                        shared memory, a row per thread group); 2 = register tiles (each thread
-                        holds a block of the message matrix and its mirror, so a message meets
-                        its partner in registers and only per-row statistics pass through shared
-                        memory).  Same arithmetic; results agree within the FP32 rounding of the
-                        row sums.  Other tiers and precisions ignore it. */
+                        = the library's choice, which is the row form (measured faster on
+                        GB300); 1 = the row form (messages in shared memory, a row per thread
+                        group); 2 = register tiles (each thread holds a block of the message
+                        matrix and its mirror, so a message meets its partner in registers and
+                        only per-row statistics pass through shared memory).  Same arithmetic;
+                        results agree within the FP32 rounding of the row sums.  Other tiers
+                        and precisions ignore it. */
 } bp4m_opts;
 
 /* Forced convergence orders the variables by posterior and picks a matching.

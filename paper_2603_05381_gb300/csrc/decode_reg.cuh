@@ -275,11 +275,22 @@ __global__ void __launch_bounds__(RegShape<NB>::NT, 1) decode_reg_kernel(const D
                 const int row = tid >> 1, half = tid & 1;
                 float m1 = ninf, m2 = ninf, acc = 0.f;
                 if (row < s) {
-                    for (int cb = half; cb < nbv; cb += 2) {
-                        const float2 o = pm[cb * PP + row];
-                        m2 = max3f(m2, o.y, fminf(m1, o.x));
-                        m1 = fmaxf(m1, o.x);
-                        acc += pa[cb * PP + row];
+                    // four partials in flight per step (independent loads), combined in order
+                    for (int cb0 = half; cb0 < nbv; cb0 += 8) {
+                        float2 o[4];
+                        float oa[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int cb = cb0 + 2 * j;
+                            o[j] = cb < nbv ? pm[cb * PP + row] : mk2(ninf, ninf);
+                            oa[j] = cb < nbv ? pa[cb * PP + row] : 0.f;
+                        }
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            m2 = max3f(m2, o[j].y, fminf(m1, o[j].x));
+                            m1 = fmaxf(m1, o[j].x);
+                            acc += oa[j];
+                        }
                     }
                 }
                 const float o1 = __shfl_xor_sync(kFull, m1, 1), o2 = __shfl_xor_sync(kFull, m2, 1);
@@ -507,7 +518,13 @@ __global__ void __launch_bounds__(RegShape<NB>::NT, 1) decode_reg_kernel(const D
                 const int row = tid >> 1, half = tid & 1;
                 float S = 0.f;
                 if (row < s)
-                    for (int cb = half; cb < nbv; cb += 2) S += ps[cb * PP + row];
+                    for (int cb0 = half; cb0 < nbv; cb0 += 8) {
+                        float o[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) o[j] = cb0 + 2 * j < nbv ? ps[(cb0 + 2 * j) * PP + row] : 0.f;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) S += o[j];
+                    }
                 S += __shfl_xor_sync(kFull, S, 1);
                 if (half == 0) {
                     // the row's output constants (rows past s: finite values for unused messages)
