@@ -86,7 +86,8 @@ constexpr size_t stream_smem_bytes_n(int stages) {
     return (kStreamPrefetch<T, CH> != 0 ? (size_t)kStreamWarpsOf<T, CH, CL> * 3 * (32 * CH) * sizeof(T) : 0) +
            (size_t)stages * kStreamWarpsOf<T, CH, CL> * kStagePitch<T, CH, CL> * sizeof(T) + sizeof(T) +
            (size_t)(32 * CH) * (sizeof(double) + 2 * sizeof(int) + sizeof(short) + 1) + 32 +
-           (sizeof(MS) == 2 ? (size_t)2 * (32 * CH) * sizeof(float) : 0) + (size_t)(32 * CH) * sizeof(short);
+           (sizeof(MS) == 2 ? (size_t)2 * (32 * CH) * sizeof(float) : 0) + (size_t)(32 * CH) * sizeof(short) +
+           (size_t)2 * (32 * CH) * sizeof(unsigned short);
 }
 // Two output stages where they fit: 227 KB per block, and for the two-block variants 113 KB.
 template <typename T, int CH, typename MS, int CL = 1>
@@ -172,6 +173,9 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
     float* nref = reinterpret_cast<float*>(reinterpret_cast<uintptr_t>(matched + LD + 15) & ~(uintptr_t)15);
     // static-partition forced convergence: factors in processing order
     short* order = reinterpret_cast<short*>(nref + (HALF ? 2 * LD : 0));
+    // posteriors judged in the update pass (see `late` below): kept counts of the rows, two
+    // 16-bit counters per word, one buffer per pass parity
+    unsigned* kcnt = reinterpret_cast<unsigned*>(order + LD);
     __shared__ int sh_item2[2], sh_s, sh_best_par, sh_best_forced, sh_improve, sh_use_best;
     __shared__ int sh_votes[2][CL];  // cluster form: each block's vote, by iteration parity
     __shared__ double sh_best_w;
@@ -249,6 +253,7 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
             matched[r] = r >= s;
             bestp[r] = -1;
             if constexpr (HALF) nref[r] = nref[LD + r] = 0.f;
+            if (r < LD / 2) kcnt[r] = kcnt[LD / 2 + r] = 0u;
         }
         if (tid == 0) {
             sh_best_w = Num<double>::pinf();
@@ -268,6 +273,25 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
         // reads the same rows (Lg, Mc, Mo once per iteration instead of twice); only the last
         // iteration, which may need forced convergence, keeps the separate decision pass
         const bool merged = !TRACE && a.decoder == 0 && a.early_exit;
+        // FP32 messages, one block per shot: the posteriors of an update are judged in the pass
+        // that produces it, each variable once, by the later of its two rows (the earlier row's
+        // message to it is then in the next incoming matrix, or in the batch's stage).  The
+        // own-output matrix is then neither read nor written, except in the pass before the
+        // last iteration, whose decisions may need forced convergence.  A variable whose
+        // posterior is bounded above by l + (own + -max_{j != r} Q_kj) <= 0 (the partner's
+        // message never exceeds minus its largest other entry) is not read at all.
+        constexpr bool LATE_OK = CL == 1 && !HALF && sizeof(T) == 4;
+        const bool late = LATE_OK && merged;
+        // kept variable v_rk (k == r: the boundary), counted at both ends; the kept column is
+        // only read for rows that keep exactly one
+        auto kept = [&](unsigned* cb, int r, int k) {
+            atomicAdd(cb + (r >> 1), 1u << ((r & 1) * 16));
+            choice[r] = k;
+            if (k != r) {
+                atomicAdd(cb + (k >> 1), 1u << ((k & 1) * 16));
+                choice[k] = r;
+            }
+        };
         for (;;) {
             const MS* Mc = Mtb[cur];
             const float* nrc = nref + cur * LD;        // references of the messages read now
@@ -291,8 +315,9 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                 if constexpr (HALF) return IO::ld(p) + nrc[r];
                 else return *p;
             };
-            const bool fuse = merged && t > 0 && t < a.T;
-            if (t > 0 && !fuse) {
+            const bool fuse = !LATE_OK && merged && t > 0 && t < a.T;
+            // with late judging the decisions of lambda^t (t < T) were taken in the last pass
+            if (t > 0 && !fuse && !(late && t < a.T)) {
                 // ---- decisions of lambda^t = l + (M[r][k] + M[k][r])
                 int ok_all = 1;
                 for (int r = row0; r < s; r += RSTEP) {
@@ -515,26 +540,43 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
             MS* Mn = Mtb[cur ^ 1];
             const int nbatch = (s + W - 1) / W;
             int ok_w = 1;  // fused decisions: every row of this warp keeps exactly one variable
+            // late judging of lambda^(t+1) in this pass (the last iteration's are judged from the
+            // own outputs, which this pass then writes)
+            const bool eval = late && t + 1 < a.T;
+            unsigned* const kc = kcnt + (t & 1) * (LD / 2);
+            if (late)
+                for (int r = tid; r < LD / 2; r += NTH) kcnt[((t + 1) & 1) * (LD / 2) + r] = 0u;
             T* const pbuf = pf + warp * 3 * LD;
             // row rr of Lg, Mc and Mo into this warp's prefetch buffer (one commit group)
-            // (16-bit message rows fill the first half of their buffer row)
-            auto prefetch = [&](int rr) {
+            // (16-bit message rows fill the first half of their buffer row).  In the FP32 one-block
+            // form the own outputs are not fetched (only the fused decisions of the other forms
+            // read them), and the prior rows alternate between the first and third buffer rows
+            // (j = the warp's row count), so that a row's priors stay in place while the next row
+            // is fetched
+            auto lslot = [&](int j) -> T* { return pbuf + ((LATE_OK && (j & 1)) ? 2 * LD : 0); };
+            auto prefetch = [&](int rr, int j) {
                 const unsigned char* src[3] = {reinterpret_cast<const unsigned char*>(Lg + (size_t)rr * LD),
                                                reinterpret_cast<const unsigned char*>(Mc + (size_t)rr * LD),
                                                reinterpret_cast<const unsigned char*>(Mo + (size_t)rr * LD)};
                 constexpr int VL = LD * (int)sizeof(T) / 16;   // 16-byte chunks per prior row
                 constexpr int VM = LD * (int)sizeof(MS) / 16;  // and per message row
+                const int nm = LATE_OK ? 2 : 3;  // the update pass reads own outputs only in the fused decisions
 #pragma unroll
                 for (int m = 0; m < 3; ++m) {
-                    unsigned char* dst = reinterpret_cast<unsigned char*>(pbuf + m * LD);
+                    if (m >= nm) break;
+                    unsigned char* dst = reinterpret_cast<unsigned char*>(m == 0 ? lslot(j) : pbuf + m * LD);
                     for (int v = lane; v < (m == 0 ? VL : VM); v += 32) cp_async16(dst + 16 * v, src[m] + 16 * v);
                 }
                 cp_async_commit();
             };
             const MS* pbx = reinterpret_cast<const MS*>(pbuf + LD);
             const MS* pbo = reinterpret_cast<const MS*>(pbuf + 2 * LD);
+            // late judging: the rows' largest and second largest Q and argmax of this pass
+            // (the bound of their messages), in the decision scratch
+            float2* rstat = reinterpret_cast<float2*>(rowacc);
+            int jrow = 0;  // rows this warp has taken in this pass
             if constexpr (PF)
-                if (row0 < s) prefetch(row0);
+                if (row0 < s) prefetch(row0, 0);
             // this block's batches b = crank, crank + CL, ...; the stage alternates with b / CL
             for (int b = crank; b < nbatch; b += CL) {
                 const int r = b * W + warp;
@@ -544,6 +586,7 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                     const T* lrow = Lg + (size_t)r * LD;
                     const MS* xrow = Mc + (size_t)r * LD;
                     MS* orow = Mo + (size_t)r * LD;
+                    const T* const pbl = lslot(jrow);  // this row's priors in the prefetch buffer
                     T lv[PFM == 1 ? CH : 1], xv[PFM == 1 ? CH : 1], ov[PFM == 1 ? CH : 1];
                     if constexpr (PF) {
                         cp_async_wait_all();
@@ -553,17 +596,17 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
 #pragma unroll
                         for (int c = 0; c < CH; ++c) {
                             const int k = lane + 32 * c;
-                            lv[c] = pbuf[k];
+                            lv[c] = pbl[k];
                             xv[c] = dx(pbx + k, k);
-                            ov[c] = down(pbo + k, r);
+                            if constexpr (!LATE_OK) ov[c] = down(pbo + k, r);
                         }
                         __syncwarp();
-                        if (r + RSTEP < s) prefetch(r + RSTEP);
+                        if (r + RSTEP < s) prefetch(r + RSTEP, jrow + 1);
                     }
                     // the row's prior, incoming message and own output at column lane + 32 c
                     auto LV = [&](int c) -> T {
                         if constexpr (PFM == 1) return lv[c];
-                        else if constexpr (PFM == 2) return pbuf[lane + 32 * c];
+                        else if constexpr (PFM == 2) return pbl[lane + 32 * c];
                         else return lrow[lane + 32 * c];
                     };
                     auto XV = [&](int c) -> T {
@@ -608,9 +651,10 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                     else
                         row_pass(std::false_type{});
                     if constexpr (PFM == 2) {
-                        // the last read of this row's buffer: the next row may replace it
+                        // the last read of this row's incoming messages (and, without late
+                        // judging, of its priors): the next row may replace them
                         __syncwarp();
-                        if (r + RSTEP < s) prefetch(r + RSTEP);
+                        if (r + RSTEP < s) prefetch(r + RSTEP, jrow + 1);
                     }
 #pragma unroll
                     for (int off = 16; off; off >>= 1) {
@@ -627,6 +671,10 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                         }
                         if (lane == 0) bcast(&choice[r], kl >= 0 ? kl : 0x7fffffff);
                         ok_w &= (cnt == 1);
+                    }
+                    if (eval && lane == 0) {
+                        rstat[r] = make_float2((float)m1, (float)m2);
+                        order[r] = (short)am;
                     }
                     T S = T(0);
 #pragma unroll
@@ -663,19 +711,68 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                         for (int c = 0; c < CH; ++c) {
                             const int k = lane + 32 * c;
                             const T out = -m1 - B2<T>::lg2(B2<T>::fma_(-cf, q[c], Aa));
-                            orow[k] = out;
+                            if (!eval) orow[k] = out;
                             srow[k] = out;
                         }
                         if ((am & 31) == lane) {
                             const T oam = -m2 - B2<T>::lg2(S - T(1));
-                            orow[am] = oam;
+                            if (!eval) orow[am] = oam;
                             srow[am] = oam;
                         }
                         __syncwarp();
+                        if constexpr (LATE_OK) {
+                            if (eval) {
+                                // lambda^(t+1) of v_rr and of v_rk for the rows k whose transposed
+                                // messages are complete in Mn (batches before b; with two stages
+                                // before b - 1: batch b - 1 is judged after the barrier below)
+                                const int kend = (NST == 2 ? b - 1 : b) * W;
+#pragma unroll
+                                for (int c = 0; c < CH; ++c) {
+                                    const int k = lane + 32 * c;
+                                    if (k < kend) {
+                                        const float own = srow[k], lk = LV(c);
+                                        const float2 st = rstat[k];
+                                        const float bnd = lk + (own + -((int)order[k] == r ? st.y : st.x));
+                                        if (bnd > -1e-3f) {
+                                            const float lam = lk + (own + __ldcg(reinterpret_cast<const float*>(Mn) + (size_t)r * LD + k));
+                                            if (lam > 0.f) kept(kc, r, k);
+                                        }
+                                    } else if (k == r) {
+                                        if (LV(c) + (srow[r] + 0.f) > 0.f) kept(kc, r, r);
+                                    }
+                                }
+                                __syncwarp();
+                            }
+                        }
                         if (lane == 0) srow[r] = T(0);  // the diagonal of Mt stays 0
                     }
+                    ++jrow;
                 }
                 __syncthreads();
+                if constexpr (LATE_OK) {
+                    if (eval && r < s) {
+                        // this batch's variables v_rk with k in the same batch (k < r): both
+                        // messages are in the stage
+                        const float* lrw = reinterpret_cast<const float*>(Lg) + (size_t)r * LD;
+                        if (lane < warp) {
+                            const int k = b * W + lane;
+                            const float lam = __ldcg(lrw + k) + (srow[k] + stage[lane * SP + r]);
+                            if (lam > 0.f) kept(kc, r, k);
+                        }
+                        // with two stages, those with k in batch b - 1, whose transposed messages
+                        // are complete now (same bound as above)
+                        if (NST == 2 && b > 0 && lane < W) {
+                            const int k = (b - 1) * W + lane;
+                            const float own = srow[k], lk = __ldcg(lrw + k);
+                            const float2 st = rstat[k];
+                            const float bnd = lk + (own + -((int)order[k] == r ? st.y : st.x));
+                            if (bnd > -1e-3f) {
+                                const float lam = lk + (own + __ldcg(reinterpret_cast<const float*>(Mn) + (size_t)r * LD + k));
+                                if (lam > 0.f) kept(kc, r, k);
+                            }
+                        }
+                    }
+                }
                 // transposed write of the batch: Mn[k][b*W + w] = stage[w][k]
                 const int r0 = b * W;
                 const int rows = min(W, s - r0);
@@ -698,6 +795,26 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
                 // the next batch writes the other one, and the barrier after its rows (which
                 // every thread reaches only after this write) protects this one
                 if (NST == 1) __syncthreads();
+            }
+            if constexpr (LATE_OK) {
+                if (eval) {
+                    // every variable of lambda^(t+1) judged: converged iff every row keeps one
+                    __syncthreads();
+                    int ok = 1;
+                    for (int r = tid; r < s; r += NTH) ok &= (((kc[r >> 1] >> ((r & 1) * 16)) & 0xFFFFu) == 1u);
+                    if (__syncthreads_and(ok)) {
+                        any_conv = true;
+                        int pc = 0;
+                        for (int r = tid; r < s; r += NTH) {
+                            const int k = choice[r];
+                            if (k >= r) pc ^= ic.tb.P[(size_t)dets[r] * n + dets[k]];
+                        }
+                        out_par = __syncthreads_count(pc) & 1;
+                        out_forced = 0;
+                        ++t;
+                        break;
+                    }
+                }
             }
             int fconv;
             if constexpr (CL > 1) {
