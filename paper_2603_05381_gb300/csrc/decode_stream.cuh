@@ -27,7 +27,11 @@ namespace cg = cooperative_groups;
 // per-block scratch slot in global memory (L2-resident for the sizes this tier meets):
 //   Lg[r][k]     prior l_rk in log2 units, -inf for k >= s          (ld = 32*CH columns)
 //   Mt[b][r][k]  incoming message M[k][r], double buffered (b = iteration parity)
-//   Mo[r][k]     the row's own outputs M[r][k], updated in place by the owning warp
+//   Mo[r][k]     the row's own outputs M[r][k], updated in place by the owning warp, for the
+//                decision passes that read whole posterior rows (the last iteration, BP4MF,
+//                full-T mode, traces; the 16-bit and cluster forms' fused decisions).  FP32
+//                BP4M with early exit, one block per shot, judges an update's posteriors in the
+//                pass that produces it instead and writes Mo only before the last iteration.
 // The diagonal of Mt is kept 0, so Q_rr = l_rr and lambda_rr = l_rr + Mo[r][r].
 // With 16-bit message storage (MS = __half or __nv_bfloat16; priors and arithmetic FP32)
 // every message leaving row r is stored relative to the row's reference r_r (its largest Q
