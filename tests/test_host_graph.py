@@ -41,6 +41,22 @@ def test_bad_arguments_are_rejected(lib):
         Graph(5, "circuit", 0.005, rounds=3)
 
 
+def test_decoder_options_are_checked_before_the_device(lib):
+    # every decoder option is validated on the host before any device work: an empty shot range
+    # with valid options returns zero counts, invalid options are rejected (no GPU needed)
+    import paper_2603_05381_gb300 as pkg
+    g = pkg.Graph(5, "circuit", 0.005)
+    for form in (0, 1, 2):
+        c = g.sample_and_decode(0, seed=1, iters=10, opts=pkg.make_opts(precision="fp32", tile_form=form))
+        assert c["shots"] == 0 and c["msg_updates"] == 0
+    bad = [dict(tile_form=3), dict(tile_form=-1), dict(stream_cluster=3), dict(forced=2), dict(alpha=0.0)]
+    for kw in bad:
+        with pytest.raises(pkg.Bp4mError):
+            g.sample_and_decode(0, seed=1, iters=10, opts=pkg.make_opts(precision="fp32", **kw))
+    with pytest.raises(pkg.Bp4mError):
+        g.sample_and_decode(0, seed=1, iters=0, opts=pkg.make_opts(precision="fp32"))
+
+
 @pytest.mark.parametrize("d", [3, 5, 7, 9])
 def test_code_capacity_tables_match_oracle(lib, d):
     from paper_2603_05381_gb300 import Graph
