@@ -81,6 +81,9 @@ def parse():
     # stream of --serve-requests requests each
     ap.add_argument("--serve-load", default="0.5")
     ap.add_argument("--serve-slots", type=int, default=4)
+    # message storage of the service's requests (the plain per-request form it is compared with
+    # is always FP32): the reduced-precision serving form by default
+    ap.add_argument("--serve-precision", default="fp16", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--no-serve", action="store_true")
     # fused multi-graph decode of circuit and code-capacity graphs (d = 5, 9, 13, 17) with
     # uneven shot counts, FP16/BF16/FP32 messages against the plain per-graph FP32 form
@@ -214,7 +217,7 @@ def run_serving(args, dev, serve_d):
 
     ds = [int(x) for x in serve_d.split(",") if x]
     rng = np.random.default_rng(SEED)
-    opts = pkg.make_opts(precision=args.precision, early_exit=True)
+    opts = pkg.make_opts(precision=args.serve_precision, early_exit=True)
     graphs, pools = [], []
     for d in ds:
         g = pkg.Graph(d, "circuit", P)
@@ -308,7 +311,8 @@ def run_serving(args, dev, serve_d):
     first = loads[0]
     return {"graphs": "rotated memory-Z circuit, d in {%s}, p=%g" % (",".join(map(str, ds)), P),
             "requests": first["requests"], "request_shots": "uniform 1..4096", "iters": T, "slots": args.serve_slots,
-            "precision": args.precision, "admission": "free device memory (no caller budget)",
+            "precision": args.serve_precision, "plain_precision": "fp32",
+            "admission": "free device memory (no caller budget)",
             "capacity_shots_per_s": cap_shots, "plain_fp32_per_request_shots_per_s": plain_shots,
             "capacity_vs_plain": cap_shots / plain_shots, "offered_load": first["offered_load"],
             "p50_ms": first["p50_ms"], "p99_ms": first["p99_ms"], "mean_ms": first["mean_ms"],
