@@ -273,9 +273,10 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
         bool any_conv = false, forced_ran = false;
         int out_par = 0, out_forced = 0, out_from_best = 0;
 
-        // BP4M with early exit: the decisions of lambda^t are taken inside the update pass that
-        // reads the same rows (Lg, Mc, Mo once per iteration instead of twice); only the last
-        // iteration, which may need forced convergence, keeps the separate decision pass
+        // BP4M with early exit, 16-bit messages or the cluster form: the decisions of lambda^t are
+        // taken inside the update pass that reads the same rows (Lg, Mc, Mo once per iteration
+        // instead of twice); only the last iteration, which may need forced convergence, keeps
+        // the separate decision pass.  The FP32 one-block form judges late instead (below)
         const bool merged = !TRACE && a.decoder == 0 && a.early_exit;
         // FP32 messages, one block per shot: the posteriors of an update are judged in the pass
         // that produces it, each variable once, by the later of its two rows (the earlier row's
