@@ -36,9 +36,7 @@ KERNEL_OF = {"tier1": "decode_smem_kernel<float, CH=32, G=1> (s <= 32)",
              "tier6": "decode_smem_kernel<float, CH=36, G=4> (s <= 144)",
              "tier7": "decode_smem_kernel<float, CH=40, G=4> (s <= 160)",
              "global": "decode_stream_kernel<float> (s > 160)"}
-# the 113..144-defect tiers in the register-tile form (--tile-form 2, or 0 when it is the
-# library's default)
-REG_TILES_DEFAULT = False
+# the 113..144-defect tiers in the register-tile form (--tile-form 2)
 KERNEL_OF_REG = {"tier5": "decode_reg_kernel<NB=32, B=4> (s <= 128)",
                  "tier6": "decode_reg_kernel<NB=24, B=6> (s <= 144)"}
 # DRAM bytes (read + write) per decoded shot of each FP32 tier kernel, from one ncu capture
@@ -68,8 +66,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     # message storage: fp32 (the configuration's, default) or the 16-bit forms (FP32 math)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
-    # FP32 tiers of 113..144 defects: 0 = the library's default, 1 = row form, 2 = register tiles
-    ap.add_argument("--tile-form", type=int, default=0, choices=[0, 1, 2])
+    # FP32 tiers of 113..144 defects, passed explicitly: 1 = row form (the library's default),
+    # 2 = register tiles
+    ap.add_argument("--tile-form", type=int, default=1, choices=[1, 2])
     # decoding-service measurement: circuit graphs of these distances (p = 0.005; the
     # default is every odd distance 5..25), requests of 1..4096 shots arriving as a Poisson
     # process at a fraction of the measured capacity
@@ -461,7 +460,7 @@ def run_ours(args, rank, world, local):
 
     # ---- roofline of the dominant kernel (largest share of event-timed decode time)
     kernel_of = dict(KERNEL_OF)
-    reg_form = args.precision == "fp32" and (args.tile_form == 2 or (args.tile_form == 0 and REG_TILES_DEFAULT))
+    reg_form = args.precision == "fp32" and args.tile_form == 2
     if reg_form:
         kernel_of.update(KERNEL_OF_REG)
     traffic_of = DRAM_BYTES_PER_SHOT_REG if reg_form else DRAM_BYTES_PER_SHOT
