@@ -29,9 +29,10 @@ namespace cg = cooperative_groups;
 //   Mt[b][r][k]  incoming message M[k][r], double buffered (b = iteration parity)
 //   Mo[r][k]     the row's own outputs M[r][k], updated in place by the owning warp, for the
 //                decision passes that read whole posterior rows (the last iteration, BP4MF,
-//                full-T mode, traces; the 16-bit and cluster forms' fused decisions).  FP32
-//                BP4M with early exit, one block per shot, judges an update's posteriors in the
-//                pass that produces it instead and writes Mo only before the last iteration.
+//                full-T mode, traces; the fused decisions of the 16-bit and cluster forms and
+//                of FP32 below 320 columns).  FP32 BP4M with early exit, one block per shot, from
+//                320 columns judges an update's posteriors in the pass that produces it instead
+//                and writes Mo only before the last iteration.
 // The diagonal of Mt is kept 0, so Q_rr = l_rr and lambda_rr = l_rr + Mo[r][r].
 // With 16-bit message storage (MS = __half or __nv_bfloat16; priors and arithmetic FP32)
 // every message leaving row r is stored relative to the row's reference r_r (its largest Q
@@ -273,19 +274,22 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
         bool any_conv = false, forced_ran = false;
         int out_par = 0, out_forced = 0, out_from_best = 0;
 
-        // BP4M with early exit, 16-bit messages or the cluster form: the decisions of lambda^t are
-        // taken inside the update pass that reads the same rows (Lg, Mc, Mo once per iteration
-        // instead of twice); only the last iteration, which may need forced convergence, keeps
-        // the separate decision pass.  The FP32 one-block form judges late instead (below)
+        // BP4M with early exit, 16-bit messages, the cluster form or FP32 below 320 columns: the
+        // decisions of lambda^t are taken inside the update pass that reads the same rows (Lg,
+        // Mc, Mo once per iteration instead of twice); only the last iteration, which may need
+        // forced convergence, keeps the separate decision pass.  The FP32 one-block form from
+        // 320 columns judges late instead (below)
         const bool merged = !TRACE && a.decoder == 0 && a.early_exit;
-        // FP32 messages, one block per shot: the posteriors of an update are judged in the pass
-        // that produces it, each variable once, by the later of its two rows (the earlier row's
-        // message to it is then in the next incoming matrix, or in the batch's stage).  The
-        // own-output matrix is then neither read nor written, except in the pass before the
-        // last iteration, whose decisions may need forced convergence.  A variable whose
-        // posterior is bounded above by l + (own + -max_{j != r} Q_kj) <= 0 (the partner's
-        // message never exceeds minus its largest other entry) is not read at all.
-        constexpr bool LATE_OK = CL == 1 && !HALF && sizeof(T) == 4;
+        // FP32 messages, one block per shot, 320 columns and more: the posteriors of an update
+        // are judged in the pass that produces it, each variable once, by the later of its two
+        // rows (the earlier row's message to it is then in the next incoming matrix, or in the
+        // batch's stage).  The own-output matrix is then neither read nor written, except in
+        // the pass before the last iteration, whose decisions may need forced convergence.  A
+        // variable whose posterior is bounded above by l + (own + -max_{j != r} Q_kj) <= 0 (the
+        // partner's message never exceeds minus its largest other entry) is not read at all.
+        // The 192- and 256-column variants keep the fused decisions: there the extra per-row
+        // work cost more time than the saved bytes.
+        constexpr bool LATE_OK = CL == 1 && !HALF && sizeof(T) == 4 && CH >= 10;
         const bool late = LATE_OK && merged;
         // kept variable v_rk (k == r: the boundary), counted at both ends; the kept column is
         // only read for rows that keep exactly one
@@ -554,10 +558,10 @@ __global__ void __launch_bounds__(W * 32, W == kStreamWarps ? kStreamBlocks<T, C
             T* const pbuf = pf + warp * 3 * LD;
             // row rr of Lg, Mc and Mo into this warp's prefetch buffer (one commit group)
             // (16-bit message rows fill the first half of their buffer row).  In the FP32 one-block
-            // form the own outputs are not fetched (only the fused decisions of the other forms
-            // read them), and the prior rows alternate between the first and third buffer rows
-            // (j = the warp's row count), so that a row's priors stay in place while the next row
-            // is fetched
+            // form from 320 columns the own outputs are not fetched (only the fused decisions of
+            // the other forms read them), and the prior rows alternate between the first and
+            // third buffer rows (j = the warp's row count), so that a row's priors stay in place
+            // while the next row is fetched
             auto lslot = [&](int j) -> T* { return pbuf + ((LATE_OK && (j & 1)) ? 2 * LD : 0); };
             auto prefetch = [&](int rr, int j) {
                 const unsigned char* src[3] = {reinterpret_cast<const unsigned char*>(Lg + (size_t)rr * LD),
